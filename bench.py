@@ -1,0 +1,396 @@
+#!/usr/bin/env python
+"""Benchmark: space-time unknowns/s of the mixed-precision refined FDM solve against the FP64 FDM.
+
+Workload (default): 256x256 squares P1 in space (65,025 interior nodes), P1 time on 512
+uniform elements, T = 1 (33,292,800 unknowns); manufactured psi = sin(pi x1) sin(pi x2)
+(1+t) e^{-it}; the load is the interpolated load (M_t,full (x) M_x) f of the nodal values
+of f = i d_t psi - Laplace psi (built on the device by st_load_nodal); psi0 = psi(., 0).
+
+One step = one full st_fdm_solve (lifting, forward transform, banded LDL^T factor and
+solve of all 512 spatial systems, back transform, FP64 residual, refinement sweeps until
+||R||/||F~|| <= 1e-12).  The inputs (533 MB) exceed the 129 MB L2, so no flush is needed.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Multi-GPU: the single-problem workload does not shard without an exchange step; N ranks
+run N independent replicas (weak scaling), timed with a barrier and the max over ranks.
+`--impl reference` times the CPU oracle (the FP64 fast diagonalisation of the paper on
+the host cores) on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+import synth  # noqa: E402
+
+METRIC = "space-time unknowns/s at <=1e-9 rel. error, mixed vs FP64 FDM; % roofline"
+UNIT = "unknowns/s"
+
+
+def parse_args(argv=None):
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--config", default="c2")
+    ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64", "fp32"])
+    ap.add_argument("--no-fp64-check", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args(argv)
+
+
+# ------------------------------------------------------------------ distributed helpers
+def dist_env():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def reduce_max(value: float, world: int, device=None) -> float:
+    """Max of a float over all ranks (identity for one rank)."""
+    if world <= 1:
+        return value
+    import torch
+    import torch.distributed as dist
+
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def barrier(world: int):
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.barrier()
+
+
+# ------------------------------------------------------------------ clocks
+class ClockSampler:
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.QUERY}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.fh, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.fh.close()
+        sms, mx, reasons = [], 0.0, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        with open(self.path) as fh:
+            for line in fh:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) < 9:
+                    continue
+                try:
+                    sms.append(float(parts[1]))
+                    mx = max(mx, float(parts[2]))
+                except ValueError:
+                    continue
+                for nm, v in zip(names, parts[5:9]):
+                    if v.lower().startswith("active"):
+                        reasons.add(nm)
+        os.unlink(self.path)
+        if not sms:
+            return None
+        return {"sm_mhz": statistics.median(sms), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sms)}
+
+
+# ------------------------------------------------------------------ roofline helpers
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as fh:
+            return json.load(fh)
+    return None
+
+
+def kernel_source_sha():
+    with open(os.path.join(ROOT, "paper_2504_07269_gb300", "csrc", "k_band.cu"), "rb") as fh:
+        return hashlib.sha256(fh.read()).hexdigest()[:16]
+
+
+def profiled_traffic(config: str):
+    """DRAM bytes per launch of the band factorisation from the committed ncu summary,
+    or None if the kernel source changed since the capture."""
+    p = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(p):
+        return None
+    with open(p) as fh:
+        d = json.load(fh)
+    e = d.get(f"band_factor_fp32_{config}")
+    if not e or e.get("k_band_sha") != kernel_source_sha():
+        return None
+    return e.get("dram_bytes_per_launch")
+
+
+# ------------------------------------------------------------------ inputs
+def make_inputs(pr, device):
+    """Nodal values of the manufactured f at every DOF time (t_0 included) and psi0 = psi(., 0)."""
+    import torch
+
+    x1, x2 = synth.interior_coords(pr.n, pr.Lx, pr.Ly)
+    # DOF times including t_0 (P1: the mesh nodes; P2: nodes and midpoints)
+    t = np.asarray(pr.t_nodes)
+    if pr.p_t == 1:
+        tf = t
+    else:
+        tf = np.empty(2 * len(t) - 1)
+        tf[0::2] = t
+        tf[1::2] = 0.5 * (t[:-1] + t[1:])
+    f = synth.f_c1(x1[None, :], x2[None, :], tf[:, None])
+    psi0 = synth.psi0_c1(x1, x2)
+    return torch.from_numpy(f).to(device), torch.from_numpy(psi0).to(device)
+
+
+# ------------------------------------------------------------------ CPU baseline (oracle)
+def cpu_oracle_sample(pr, n_solves=None, workers=None):
+    """Times the CPU oracle's FP64 FDM on a bounded sample of the workload: both dense time
+    transforms in full and `n_solves` of the n_t sparse-direct spatial solves (process pool,
+    one BLAS thread per worker); the solve time is extrapolated to all n_t systems."""
+    from oracle import cpu_fdm, fe_space, fe_time, timedec
+
+    workers = workers or os.cpu_count()
+    n_solves = n_solves or max(workers, 8)
+    M_t, B_t, m_t, _ = fe_time.assemble_time(pr.p_t, pr.t_nodes)
+    X, s, Y, _ = timedec.fdm_decomposition(M_t, B_t)
+    F = synth.cn01((pr.n_t, pr.n_x), seed=pr.seed)
+    t0 = time.perf_counter()
+    G = Y @ F
+    _ = X @ G
+    t_xf = time.perf_counter() - t0
+    idx = np.linspace(0, pr.n_t - 1, n_solves).astype(int)
+    t0 = time.perf_counter()
+    cpu_fdm.spatial_solves(pr.n, s[idx], G[idx], pr.Lx, pr.Ly, workers=workers)
+    t_sol = time.perf_counter() - t0
+    est = t_xf + t_sol * pr.n_t / len(idx)
+    return {"value": pr.unknowns / est, "unit": UNIT, "cores": workers, "kind": "oracle",
+            "sample": (f"CPU FP64 FDM (numpy eig, SuperLU per eigen-index): both transforms in full, "
+                       f"{len(idx)} of {pr.n_t} spatial solves on a {workers}-process pool, extrapolated; "
+                       f"measured {t_xf + t_sol:.1f} s, estimated full solve {est:.1f} s")}
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return 0
+    pr = synth.config_problem(args.config)
+    vals = []
+    for i in range(args.warmup + args.steps):
+        r = cpu_oracle_sample(pr)
+        if i >= args.warmup:
+            vals.append(r["value"])
+    v = statistics.median(vals)
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * pr.unknowns / v,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": _config(pr, args),
+            "cpu_baseline": dict(r, value=v),
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+    return 0
+
+
+def _config(pr, args):
+    return {"workload": f"{pr.n}x{pr.n} squares P1 space ({pr.n_x} nodes), P{pr.p_t} time {len(pr.t_nodes) - 1} "
+                        f"uniform elements (n_t={pr.n_t}), T={pr.t_nodes[-1]:g}; {pr.unknowns} unknowns",
+            "name": pr.name, "precision": args.precision, "tol": 1e-12, "n_x": pr.n_x, "n_t": pr.n_t,
+            "unknowns": pr.unknowns, "l2_flush": "inputs (533 MB c128 load) larger than the 129 MB L2",
+            "parallelism": "replicas" if args.gpus > 1 else "single GPU"}
+
+
+# ------------------------------------------------------------------ our solver
+def run_ours(args):
+    import torch
+
+    rank, world, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl", init_method="env://")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    from paper_2504_07269_gb300 import stfdm
+
+    pr = synth.config_problem(args.config)
+    t0 = time.perf_counter()
+    h = stfdm.setup_problem(pr.n, pr.p_t, pr.t_nodes, Lx=pr.Lx, Ly=pr.Ly, device=local)
+    setup_s = time.perf_counter() - t0
+    f_nodal, p0 = make_inputs(pr, dev)
+    F = stfdm.st_load_nodal(h, f_nodal)
+    del f_nodal
+    dt = torch.complex64 if args.precision == "fp32" else torch.complex128
+    F = F.to(dt)
+    p0 = p0.to(dt)
+    psi = torch.empty_like(F)
+    info = {}
+
+    def step():
+        nonlocal info
+        _, info = stfdm.st_fdm_solve(h, F, p0, psi=psi, precision=args.precision)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    clk = ClockSampler(local)
+    clk.start()
+    barrier(world)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(args.steps):
+        step()
+    e1.record()
+    torch.cuda.synchronize()
+    barrier(world)
+    clocks = clk.stop()
+    t_ms = e0.elapsed_time(e1) / args.steps
+    t_ms = reduce_max(t_ms, world, dev)
+    value = world * pr.unknowns / (t_ms * 1e-3)
+    sweeps = int(info.get("sweeps", 1)) if info else 1
+    # our kernels per step: A_x psi0, (sweeps + 1) x (residual + reduction), sweeps x (2 transforms + band),
+    # final psi0 add   (mixed);  FP64/FP32: A_x psi0, 2 transforms, band
+    launches_per_step = (1 + 2 * (sweeps + 1) + 3 * sweeps + 1) if args.precision == "mixed" else 4
+
+    # ---- end to end through the C ABI with host buffers (H2D of F and psi0, D2H of psi)
+    Fh = F.cpu().pin_memory()
+    p0h = p0.cpu().pin_memory()
+    psih = torch.empty(F.shape, dtype=dt).pin_memory()
+    Fd = torch.empty_like(F)
+    p0d = torch.empty_like(p0)
+
+    def e2e_step():
+        Fd.copy_(Fh, non_blocking=True)
+        p0d.copy_(p0h, non_blocking=True)
+        stfdm.st_fdm_solve(h, Fd, p0d, psi=psi, precision=args.precision, want_info=False)
+        psih.copy_(psi, non_blocking=True)
+
+    e2e_step()
+    torch.cuda.synchronize()
+    barrier(world)
+    e0.record()
+    for _ in range(args.steps):
+        e2e_step()
+    e1.record()
+    torch.cuda.synchronize()
+    e2e_ms = reduce_max(e0.elapsed_time(e1) / args.steps, world, dev)
+    h2d = Fh.numel() * Fh.element_size() + p0h.numel() * p0h.element_size()
+    d2h = psih.numel() * psih.element_size()
+
+    # ---- error against the FP64 FDM on the same inputs
+    err = None
+    fp64_value = None
+    if not args.no_fp64_check and args.precision != "fp64":
+        ref = torch.empty(F.shape, dtype=torch.complex128, device=dev)
+        F64, p064 = F.to(torch.complex128), p0.to(torch.complex128)
+        stfdm.st_fdm_solve(h, F64, p064, psi=ref, precision="fp64")
+        torch.cuda.synchronize()
+        e0.record()
+        stfdm.st_fdm_solve(h, F64, p064, psi=ref, precision="fp64", want_info=False)
+        e1.record()
+        torch.cuda.synchronize()
+        fp64_value = pr.unknowns / (e0.elapsed_time(e1) * 1e-3)
+        stfdm.st_fdm_solve(h, F, p0, psi=psi, precision=args.precision, want_info=False)
+        err = float(torch.linalg.vector_norm(psi.to(torch.complex128) - ref) / torch.linalg.vector_norm(ref))
+        del ref, F64, p064
+
+    # ---- roofline of the dominant kernel: the banded LDL^T factor-and-solve (FP32 / FP64)
+    kprec = "fp64" if args.precision == "fp64" else "fp32"
+    kdt = torch.complex128 if kprec == "fp64" else torch.complex64
+    G0 = torch.from_numpy(synth.cn01((pr.n_t, pr.n_x), seed=11)).to(dev).to(kdt)
+    Gw = torch.empty_like(G0)
+    times = []
+    for r in range(3):
+        Gw.copy_(G0)
+        torch.cuda.synchronize()
+        e0.record()
+        stfdm.st_spatial_solve(h, kprec, Gw, Gw)
+        e1.record()
+        torch.cuda.synchronize()
+        times.append(e0.elapsed_time(e1) * 1e-3)
+    tk = statistics.median(times)
+    b = pr.n - 1 + 1
+    flops = 8.0 * pr.n_t * pr.n_x * b * b / 2.0      # complex MAC = 8 real flops; n_x b^2/2 per system
+    props = torch.cuda.get_device_properties(dev)
+    max_mhz = (clocks or {}).get("sm_max_mhz") or (measured_peaks() or {}).get("sm_max_mhz", 2070.0)
+    lanes = 128 if kprec == "fp32" else 2             # FP32 / FP64 FMA lanes per SM per clock
+    peak = props.multi_processor_count * lanes * 2 * max_mhz * 1e6 / 1e12
+    achieved = flops / tk / 1e12
+    roof = {"bound": "alu", "kernel": f"k_band_factor_solve<{'float' if kprec == 'fp32' else 'double'},16>",
+            "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+            "traffic": profiled_traffic(args.config), "launch_ms": tk * 1e3,
+            "peak_basis": f"{props.multi_processor_count} SMs x {lanes} {kprec.upper()} FMA lanes x 2 x {max_mhz:.0f} MHz "
+                          "(derived, max SM clock)"}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        try:
+            cpu = cpu_oracle_sample(pr)
+        except Exception as ex:  # the baseline is reported, not required
+            cpu = {"error": str(ex)}
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": t_ms, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": {"mixed": "c64+f64", "fp64": "f64", "fp32": "f32"}[args.precision],
+                "data": "synthetic (manufactured solution, interpolated load)", "config": _config(pr, args),
+                "err_vs_fp64": err, "fp64_fdm_unknowns_per_s": fp64_value, "sweeps": sweeps,
+                "final_rel_residual": info.get("rel_residual") if info else None,
+                "setup_s": setup_s, "kappa_x": h.kappa,
+                "e2e": {"value": world * pr.unknowns / (e2e_ms * 1e-3), "unit": UNIT, "h2d_bytes_per_step": h2d,
+                        "d2h_bytes_per_step": d2h},
+                "gpu_launches": launches_per_step * args.steps,
+                "roofline": roof, "cpu_baseline": cpu, "clocks": clocks}
+        print(json.dumps(line))
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.destroy_process_group()
+    return 0
+
+
+def main(argv=None):
+    args = parse_args(argv)
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,215 @@
+/*
+ * stfdm.h -- C ABI of the GB300 space-time fast-diagonalisation solver for the
+ * linear Schroedinger equation  i d_t psi - Laplace_x psi = f  on Omega x (0,T),
+ * psi = 0 on the boundary of Omega, psi(., 0) = psi0  (Section 1, eq. (1)).
+ *
+ * Discretisation (Section 3): conforming space-time Galerkin FEM with
+ * tensor-product continuous piecewise polynomials, Q^p_h = S_hx (x) S_ht,
+ * giving the global system (eq. LGS)
+ *
+ *        K psi = f,     K = i B_t (x) M_x + M_t (x) A_x,
+ *
+ * with spatial mass/stiffness M_x, A_x (eq. matrix_x) and temporal mass and
+ * first-derivative matrices M_t, B_t (eq. matrix_t); the temporal DOF at t_0
+ * is removed (trial space = test space = Q^p_{h,0,}).  The initial condition
+ * enters by the lifting psi = psi_hat + psi0 (Section 3, eq. VF_FEM), which
+ * changes the right-hand side to  F~ = F - m_t (x) A_x psi0  with
+ * m_t[k] = int_0^T phi_k dt.
+ *
+ * Solver (Section 3, fast diagonalisation choice):
+ *   step 1  (i B_t)^{-1} M_t = X_t S_t X_t^{-1},  S_t = diag(s_k),  Y_t = X_t^{-1} (i B_t)^{-1}
+ *   step 2  G = Y_t F~                          (dense n_t x n_t contraction)
+ *   step 3  (M_x + s_k A_x) w_k = g_k, k = 1..n_t, independent (eq. LGS_x, zero sum term)
+ *   step 4  Psi = X_t W  (+ psi0)
+ *
+ * Data layout of every space-time array: row-major (n_t, n_x), row = time DOF
+ * t_1..t_{n_t} (for P2 in time: t_{1/2}, t_1, t_{3/2}, ...), column = interior
+ * spatial node in lexicographic order with x1 fastest; complex numbers are
+ * interleaved (re, im), i.e. the memory layout of C99 double complex /
+ * torch.complex128 ("c128") or float complex / torch.complex64 ("c64").
+ * Spatial vectors (psi0) have n_x entries in the same node order.
+ *
+ * Ownership: handles (st_time, st_space, st_fdm) are opaque and owned by the
+ * library until the matching st_destroy_*.  All space-time arrays passed to
+ * the solve entry points are DEVICE pointers owned by the caller; the library
+ * never frees them.  Handle-internal device workspace is allocated by the
+ * library (at setup, or at the first solve that needs it) and freed by
+ * st_destroy_fdm.  Every device entry point is asynchronous on the given CUDA
+ * stream (a cudaStream_t passed as void*, NULL = legacy default stream) except
+ * where it says it synchronises; two calls on the same handle must not run
+ * concurrently (they share the handle's workspace).
+ *
+ * Errors: no C++ exception crosses this ABI.  Every entry point returns an
+ * st_status (0 = ST_OK, negative = error); st_last_error_message() gives a
+ * human-readable detail of the last error of the calling thread.
+ */
+#ifndef STFDM_H
+#define STFDM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef int st_status;
+
+#define ST_OK                    0
+#define ST_ERR_ARG              -1   /* invalid argument (NULL, size, range, unsupported combination) */
+#define ST_ERR_OOM              -2   /* host or device allocation failed */
+#define ST_ERR_CUDA             -3   /* a CUDA runtime call or kernel launch failed */
+#define ST_ERR_ILL_CONDITIONED  -4   /* kappa_2(X_t) > kappa_max, or some Im s_k clearly > 0 */
+#define ST_ERR_ZERO_PIVOT       -5   /* a pivot of an LDL^T factorisation was zero or not finite */
+#define ST_ERR_NOT_CONVERGED    -6   /* eigen-iteration or refinement did not reach its tolerance */
+#define ST_ERR_TIMEOUT          -7   /* a bounded device-side wait expired */
+#define ST_ERR_UNSUPPORTED      -8   /* not built for this device / configuration */
+
+/* precision modes of a solve */
+#define ST_FP64   0   /* c128 in/out, every step in FP64 */
+#define ST_FP32   1   /* c64 in/out, every step in FP32 (complex64); error stated, not refined */
+#define ST_MIXED  2   /* c128 in/out: complex-FP32 FDM sweeps refined on an FP64 Kronecker residual */
+
+/* time transform selectors for st_time_transform (step 2 / step 4 / adjoint) */
+#define ST_XFORM_Y    0   /* out = Y_t in        (forward transform, step 2) */
+#define ST_XFORM_X    1   /* out = X_t in        (back transform, step 4)    */
+#define ST_XFORM_XT   2   /* out = X_t^T in      (adjoint, first transform)  */
+#define ST_XFORM_YT   3   /* out = Y_t^T in      (adjoint, last transform)   */
+
+typedef struct st_time st_time;
+typedef struct st_space st_space;
+typedef struct st_fdm st_fdm;
+
+typedef struct {
+    double kappa_max;   /* reject X_t with kappa_2 above this; <= 0 selects 1e10 (Section 3: X_t must be regular) */
+    int device;         /* CUDA device ordinal for the handle's device data; < 0 = the current device */
+    int host_threads;   /* threads for the host FP64 setup; <= 0 = hardware concurrency */
+} st_setup_opts;
+
+typedef struct {
+    int precision;      /* ST_FP64, ST_FP32 or ST_MIXED */
+    double tol;         /* ST_MIXED: stop when ||F~ - K psi_hat||_2 / ||F~||_2 <= tol; <= 0 selects 1e-12 */
+    int max_sweeps;     /* ST_MIXED: at most this many FDM sweeps; <= 0 selects 12 */
+    int keep_factors;   /* ST_MIXED: 1 = store all n_t LDL^T factors and reuse them in later sweeps
+                           when they fit the memory budget, 0 = refactor every sweep, -1 = automatic */
+    int fixed_sweeps;   /* ST_MIXED: > 0 runs exactly this many sweeps with no host synchronisation
+                           (no convergence test; the final residual is still reported) */
+} st_solve_opts;
+
+typedef struct {
+    int sweeps;                  /* FDM sweeps run (1 for ST_FP64 / ST_FP32) */
+    int factors_kept;            /* 1 if the LDL^T factors were reused across sweeps */
+    double rel_residual;         /* final ||F~ - K psi_hat|| / ||F~|| (computed for ST_MIXED; -1 otherwise) */
+    double residual_history[16]; /* rel. residual before each sweep (ST_MIXED), then the final one */
+    double kappa_x;              /* kappa_2(X_t) */
+    double min_neg_im_shift;     /* min_k (-Im s_k); >= 0 up to rounding */
+    double setup_seconds;        /* host time of st_fdm_setup's FP64 decomposition */
+} st_solve_info;
+
+/* ------------------------------------------------------------------ status */
+const char* st_status_string(st_status s);
+const char* st_last_error_message(void);
+int st_abi_version(void);   /* returns STFDM_ABI_VERSION of the built library */
+#define STFDM_ABI_VERSION 1
+
+/* ------------------------------------------------------------------ assembly (host) */
+/* Temporal matrices of eq. (matrix_t), Section 3.  p_t in {1, 2}: continuous piecewise
+ * linear / quadratic Lagrange elements on 0 = t_0 < t_1 < ... < t_{N_t} = T (t_nodes has
+ * N_t + 1 strictly increasing host doubles, t_nodes[0] = 0).  Builds the reduced (t_0 DOF
+ * removed) banded M_t, B_t (half bandwidth p_t), n_t = p_t N_t, and m_t.  *out is owned by
+ * the library.  Errors: ST_ERR_ARG (bad p_t, N_t < 1, nodes not increasing / t0 != 0). */
+st_status st_assemble_time(int p_t, int N_t, const double* t_nodes, st_time** out);
+/* Dense copies for inspection (host, row-major n_t x n_t; any pointer may be NULL). */
+st_status st_time_get(const st_time* t, int* n_t, double* M_t, double* B_t, double* m_t, double* dof_times);
+
+/* Spatial matrices of eq. (matrix_x): P1 on (0,Lx) x (0,Ly) split into n_squares^2 rectangles,
+ * each cut along its SW-NE diagonal; interior (Dirichlet) DOFs only, n_x = (n_squares-1)^2,
+ * lexicographic x1 fastest, half bandwidth b = n_squares.  The matrices are 7-point stencils:
+ * M_x: centre h1 h2/2, W/E/S/N/SW/NE h1 h2/12;  A_x: centre 2(h2/h1 + h1/h2), W/E -h2/h1,
+ * S/N -h1/h2, SW/NE 0.  Errors: ST_ERR_ARG (n_squares < 2, non-positive lengths). */
+st_status st_assemble_space(int n_squares, double Lx, double Ly, st_space** out);
+/* coeffs[8] = {Mc, Mw(=Me), Ms(=Mn), Mdiag(SW/NE), Ac, Aw, As, Adiag}; m = n_squares - 1. */
+st_status st_space_get(const st_space* s, int* m, int* n_x, double* coeffs);
+
+/* Step 1 on the host, no device needed (Section 3, fast diagonalisation): X_t (unit 2-norm
+ * columns), s (eigenvalues), Y_t = X_t^{-1} (i B_t)^{-1}, kappa_2(X_t).  X, Y: host
+ * complex128 row-major n_t x n_t; s: host complex128 n_t; any output may be NULL.
+ * Errors: ST_ERR_NOT_CONVERGED (QR iteration), ST_ERR_ARG. */
+st_status st_time_decompose(const st_time* t, int host_threads, double* X, double* s, double* Y,
+                            double* kappa2);
+
+/* ------------------------------------------------------------------ setup */
+/* Builds the solver handle: step 1 in FP64 on the host (timed separately), then uploads
+ * X_t, Y_t, X_t^T, Y_t^T, s_k, Y_t m_t (FP64 and FP32 copies) and the band coefficients to the
+ * device.  Errors: ST_ERR_ILL_CONDITIONED (kappa_2 > kappa_max, or some Im s_k > 1e-8 max|s|:
+ * in exact arithmetic Im s_k < 0, which keeps every C_k = M_x + s_k A_x pivot-free; shifts with
+ * |Im s_k| at rounding level are accepted and zero pivots are reported by the solves),
+ * ST_ERR_CUDA, ST_ERR_OOM. */
+st_status st_fdm_setup(const st_time* t, const st_space* s, const st_setup_opts* opts, st_fdm** out);
+st_status st_fdm_get(const st_fdm* h, int* n_t, int* n_x, int* m, double* kappa2, double* min_neg_im_shift);
+
+/* ------------------------------------------------------------------ solves (device) */
+/* The full solve, steps 2-4 (+ lifting, + refinement for ST_MIXED).
+ * F: device (n_t, n_x) load vector (c128 for ST_FP64/ST_MIXED, c64 for ST_FP32).
+ * psi0: device n_x initial values at the interior nodes (same complex type) or NULL (= 0).
+ * psi: device (n_t, n_x) output, the nodal values of psi_h at t_1..t_{n_t}; must not alias F.
+ * info: may be NULL.  ST_MIXED (unless fixed_sweeps > 0) synchronises the stream once per
+ * sweep to read the residual norm.  Errors: ST_ERR_ARG, ST_ERR_CUDA, ST_ERR_OOM,
+ * ST_ERR_ZERO_PIVOT, ST_ERR_NOT_CONVERGED (info is still filled). */
+st_status st_fdm_solve(st_fdm* h, const void* F, const void* psi0, void* psi,
+                       const st_solve_opts* opts, st_solve_info* info, void* stream);
+
+/* FP64 Kronecker residual R = F~ - K (psi - 1 (x) psi0) with F~ = F - m_t (x) A_x psi0
+ * (eq. LGS; c128 arrays, psi0 may be NULL).  R may be NULL (norm only).  rel_norm (host, may be
+ * NULL) receives ||R||_2 / ||F~||_2; when it is non-NULL the call synchronises the stream. */
+st_status st_residual(st_fdm* h, const void* F, const void* psi0, const void* psi, void* R,
+                      double* rel_norm, void* stream);
+
+/* Adjoint solve K^H lambda = G with the same FDM machinery:
+ * K^{-H} = conj o (Y_t^T (x) I) blockdiag(C_k^{-1}) (X_t^T (x) I) o conj, C_k = M_x + s_k A_x
+ * (complex symmetric, so C_k^{-T} = C_k^{-1} reuses the forward factors).
+ * G, lambda: device (n_t, n_x), c128 for ST_FP64/ST_MIXED (ST_MIXED refines on the FP64 adjoint
+ * residual), c64 for ST_FP32. */
+st_status st_adjoint_solve(st_fdm* h, const void* G, void* lambda, const st_solve_opts* opts,
+                           st_solve_info* info, void* stream);
+
+/* Gradient of a loss J(psi) with respect to psi0 from grad_psi = dJ/dpsi-bar (PyTorch's complex
+ * convention) and grad_F = K^{-H} grad_psi:  grad_psi0 = sum_l grad_psi[l,:] - A_x (m_t^T grad_F).
+ * c128 device arrays; grad_psi0 has n_x entries. */
+st_status st_adjoint_lift(st_fdm* h, const void* grad_psi, const void* grad_F, void* grad_psi0,
+                          void* stream);
+
+/* Many independent problems of uneven size in one call: each phase (transforms, banded
+ * factor-and-solve) is one grouped persistent launch over a cost-sorted work list; with
+ * ST_FP64 / fixed_sweeps > 0 the whole call can be captured in a CUDA graph.  Arrays of
+ * `count` handles and device pointers as in st_fdm_solve; infos may be NULL or hold `count`
+ * entries. */
+st_status st_fdm_solve_batched(st_fdm* const* hs, int count, const void* const* F,
+                               const void* const* psi0, void* const* psi,
+                               const st_solve_opts* opts, st_solve_info* infos, void* stream);
+
+/* ------------------------------------------------------------------ single steps (device) */
+/* Step 2 / step 4 / adjoint transforms: out = T in with T selected by `which` (ST_XFORM_*),
+ * in/out (n_t, n_x) device arrays, c128 (precision ST_FP64) or c64 (ST_FP32; ST_MIXED = the
+ * 3xTF32 tensor-core path on c64 data).  Must not alias. */
+st_status st_time_transform(st_fdm* h, int which, int precision, const void* in, void* out, void* stream);
+
+/* Step 3: W[k,:] = (M_x + s_k A_x)^{-1} G[k,:] for all k by pivot-free banded LDL^T
+ * (complex symmetric, no conjugation), factor and solve in one launch.  G, W: (n_t, n_x)
+ * device arrays (c128 for ST_FP64, c64 for ST_FP32/ST_MIXED); W may alias G. */
+st_status st_spatial_solve(st_fdm* h, int precision, const void* G, void* W, void* stream);
+
+/* Interpolated load F = (M_t,full (x) M_x) f_nodal (rows t_1.. of the full temporal mass
+ * matrix applied to nodal values f at all DOF times t_0, t_1, ...): f_nodal (n_t + 1, n_x) c128,
+ * F (n_t, n_x) c128 (device).  Assembly helper, not part of the solve. */
+st_status st_load_nodal(st_fdm* h, const void* f_nodal, void* F, void* stream);
+
+/* ------------------------------------------------------------------ teardown */
+void st_destroy_time(st_time* t);
+void st_destroy_space(st_space* s);
+void st_destroy_fdm(st_fdm* h);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* STFDM_H */

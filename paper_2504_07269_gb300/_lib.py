@@ -1,0 +1,114 @@
+"""ctypes loader of libstfdm.so and the C structs of include/stfdm.h.
+
+Fails loudly when the library is missing: there is no fallback path.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+from . import build as _build
+
+c_int = ctypes.c_int
+c_double = ctypes.c_double
+c_void_p = ctypes.c_void_p
+c_char_p = ctypes.c_char_p
+
+ST_OK = 0
+ST_ERR_ARG = -1
+ST_ERR_OOM = -2
+ST_ERR_CUDA = -3
+ST_ERR_ILL_CONDITIONED = -4
+ST_ERR_ZERO_PIVOT = -5
+ST_ERR_NOT_CONVERGED = -6
+ST_ERR_TIMEOUT = -7
+ST_ERR_UNSUPPORTED = -8
+
+ST_FP64 = 0
+ST_FP32 = 1
+ST_MIXED = 2
+
+ST_XFORM_Y = 0
+ST_XFORM_X = 1
+ST_XFORM_XT = 2
+ST_XFORM_YT = 3
+
+
+class st_setup_opts(ctypes.Structure):
+    _fields_ = [("kappa_max", c_double), ("device", c_int), ("host_threads", c_int)]
+
+
+class st_solve_opts(ctypes.Structure):
+    _fields_ = [("precision", c_int), ("tol", c_double), ("max_sweeps", c_int), ("keep_factors", c_int),
+                ("fixed_sweeps", c_int)]
+
+
+class st_solve_info(ctypes.Structure):
+    _fields_ = [("sweeps", c_int), ("factors_kept", c_int), ("rel_residual", c_double),
+                ("residual_history", c_double * 16), ("kappa_x", c_double), ("min_neg_im_shift", c_double),
+                ("setup_seconds", c_double)]
+
+
+# name -> (restype, argtypes); every entry point declared in include/stfdm.h
+SIGNATURES = {
+    "st_status_string": (c_char_p, [c_int]),
+    "st_last_error_message": (c_char_p, []),
+    "st_abi_version": (c_int, []),
+    "st_assemble_time": (c_int, [c_int, c_int, ctypes.POINTER(c_double), ctypes.POINTER(c_void_p)]),
+    "st_time_get": (c_int, [c_void_p, ctypes.POINTER(c_int), c_void_p, c_void_p, c_void_p, c_void_p]),
+    "st_assemble_space": (c_int, [c_int, c_double, c_double, ctypes.POINTER(c_void_p)]),
+    "st_space_get": (c_int, [c_void_p, ctypes.POINTER(c_int), ctypes.POINTER(c_int), c_void_p]),
+    "st_time_decompose": (c_int, [c_void_p, c_int, c_void_p, c_void_p, c_void_p, ctypes.POINTER(c_double)]),
+    "st_fdm_setup": (c_int, [c_void_p, c_void_p, ctypes.POINTER(st_setup_opts), ctypes.POINTER(c_void_p)]),
+    "st_fdm_get": (c_int, [c_void_p, ctypes.POINTER(c_int), ctypes.POINTER(c_int), ctypes.POINTER(c_int),
+                           ctypes.POINTER(c_double), ctypes.POINTER(c_double)]),
+    "st_fdm_solve": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, ctypes.POINTER(st_solve_opts),
+                             ctypes.POINTER(st_solve_info), c_void_p]),
+    "st_residual": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, ctypes.POINTER(c_double), c_void_p]),
+    "st_adjoint_solve": (c_int, [c_void_p, c_void_p, c_void_p, ctypes.POINTER(st_solve_opts),
+                                 ctypes.POINTER(st_solve_info), c_void_p]),
+    "st_adjoint_lift": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]),
+    "st_fdm_solve_batched": (c_int, [ctypes.POINTER(c_void_p), c_int, ctypes.POINTER(c_void_p),
+                                     ctypes.POINTER(c_void_p), ctypes.POINTER(c_void_p),
+                                     ctypes.POINTER(st_solve_opts), ctypes.POINTER(st_solve_info), c_void_p]),
+    "st_time_transform": (c_int, [c_void_p, c_int, c_int, c_void_p, c_void_p, c_void_p]),
+    "st_spatial_solve": (c_int, [c_void_p, c_int, c_void_p, c_void_p, c_void_p]),
+    "st_load_nodal": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p]),
+    "st_destroy_time": (None, [c_void_p]),
+    "st_destroy_space": (None, [c_void_p]),
+    "st_destroy_fdm": (None, [c_void_p]),
+}
+
+_LIB = None
+
+
+def lib():
+    """The loaded library (built in-tree by __graft_entry__.build())."""
+    global _LIB
+    if _LIB is None:
+        path = _build.LIB
+        if not os.path.exists(path):
+            raise RuntimeError(
+                f"stfdm CUDA library not found at {path}: run __graft_entry__.build() "
+                "(there is no CPU fallback)")
+        L = ctypes.CDLL(path)
+        for name, (res, args) in SIGNATURES.items():
+            fn = getattr(L, name)
+            fn.restype = res
+            fn.argtypes = args
+        _LIB = L
+    return _LIB
+
+
+class StfdmError(RuntimeError):
+    def __init__(self, status: int, where: str):
+        L = lib()
+        msg = L.st_last_error_message()
+        super().__init__(f"{where}: {L.st_status_string(status).decode()} ({status}): "
+                         f"{msg.decode() if msg else ''}")
+        self.status = status
+
+
+def check(status: int, where: str):
+    if status != ST_OK:
+        raise StfdmError(status, where)

@@ -1,0 +1,686 @@
+// C ABI of the solver: handle setup (step 1 on the host, upload), the full solve in
+// FP64 / FP32 / mixed precision with FP64 iterative refinement, the FP64 residual, the
+// adjoint solve, single-step entry points and the batched solve.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "device.cuh"
+
+namespace stfdm {
+
+// launchers implemented in the kernel files
+cudaError_t launch_stencil_A(const SpaceMats& sm, const void* in, bool in_c64, const double2* add, double sign,
+                             double2* out, cudaStream_t st);
+int residual_num_partials(int n_t, int n_x);
+cudaError_t launch_residual(const SpaceMats& sm, int n_t, const double* Mb, const double* Bb, double bsign,
+                            const double2* F, const double2* apsi0, const double* m_t, const double2* U,
+                            const double2* psi0, double2* R, double* partials, double* scalars, cudaStream_t st);
+cudaError_t launch_add_row(int n_t, int n_x, void* psi, const void* psi0, bool c64, cudaStream_t st);
+cudaError_t launch_load_nodal(const SpaceMats& sm, int n_t, const double* Mb, const double* Mfull0,
+                              const double2* f, double2* F, cudaStream_t st);
+cudaError_t launch_colsums(int n_t, int n_x, const double2* U1, const double2* U2, const double* w, double2* out1,
+                           double2* out2, cudaStream_t st);
+
+}  // namespace stfdm
+
+using namespace stfdm;
+
+#define CUDA_TRY(expr)                                                                       \
+    do {                                                                                     \
+        cudaError_t _e = (expr);                                                             \
+        if (_e != cudaSuccess)                                                               \
+            return fail(ST_ERR_CUDA, std::string(#expr) + ": " + cudaGetErrorString(_e));    \
+    } while (0)
+
+namespace {
+
+st_status dev_alloc(void** p, size_t bytes, const char* what) {
+    *p = nullptr;
+    if (bytes == 0) return ST_OK;
+    cudaError_t e = cudaMalloc(p, bytes);
+    if (e != cudaSuccess) {
+        *p = nullptr;
+        cudaGetLastError();
+        return fail(e == cudaErrorMemoryAllocation ? ST_ERR_OOM : ST_ERR_CUDA,
+                    std::string("cudaMalloc(") + what + ", " + std::to_string(bytes) + " B): " + cudaGetErrorString(e));
+    }
+    return ST_OK;
+}
+
+// grow a workspace buffer (contents not preserved)
+st_status grow(void*& p, size_t& have, size_t need, const char* what) {
+    if (need <= have && p) return ST_OK;
+    if (p) cudaFree(p);
+    p = nullptr;
+    have = 0;
+    st_status s = dev_alloc(&p, need, what);
+    if (s == ST_OK) have = need;
+    return s;
+}
+
+template <typename T>
+st_status upload(T** dst, const void* src, size_t bytes, const char* what) {
+    st_status s = dev_alloc((void**)dst, bytes, what);
+    if (s != ST_OK) return s;
+    CUDA_TRY(cudaMemcpy(*dst, src, bytes, cudaMemcpyHostToDevice));
+    return ST_OK;
+}
+
+struct DeviceGuard {
+    int prev = -1;
+    explicit DeviceGuard(int dev) {
+        cudaGetDevice(&prev);
+        if (dev >= 0 && dev != prev) cudaSetDevice(dev);
+    }
+    ~DeviceGuard() {
+        if (prev >= 0) cudaSetDevice(prev);
+    }
+};
+
+inline cudaStream_t S(void* stream) { return reinterpret_cast<cudaStream_t>(stream); }
+
+void free_handle(st_fdm* h) {
+    if (!h) return;
+    DeviceGuard g(h->device);
+    for (int i = 0; i < 4; ++i) {
+        cudaFree(h->xf64[i]);
+        cudaFree(h->xf32[i]);
+        cudaFree(h->xf_tf32[i][0]);
+        cudaFree(h->xf_tf32[i][1]);
+    }
+    cudaFree(h->s64);
+    cudaFree(h->s32);
+    cudaFree(h->Ym64);
+    cudaFree(h->dt.Mb);
+    cudaFree(h->dt.Bb);
+    cudaFree(h->dt.BTb);
+    cudaFree(h->dt.Mfull0);
+    cudaFree(h->dt.m);
+    cudaFree(h->ws_big);
+    cudaFree(h->ws_g32);
+    cudaFree(h->ws_win);
+    cudaFree(h->ws_L);
+    cudaFree(h->ws_D);
+    cudaFree(h->ws_vec);
+    cudaFree(h->ws_red);
+    cudaFree(h->ws_status);
+    delete h;
+}
+
+// ------------------------------------------------------------------ transforms
+template <typename TA, typename TB, typename TC, typename TACC>
+st_status xform(const TA* A2, int n_t, int n_x, const void* in, void* out, int conj_b, int conj_out,
+                int accumulate, const double* b_scale, const double* out_scale, const void* add_row,
+                const double2* r1_u, const double2* r1_v, cudaStream_t st) {
+    XformArgs<TA, TB, TC> a;
+    a.M = n_t;
+    a.N = n_x;
+    a.K = n_t;
+    a.A = reinterpret_cast<const C<TA>*>(A2);
+    a.lda = n_t;
+    a.B = reinterpret_cast<const C<TB>*>(in);
+    a.ldb = n_x;
+    a.Cm = reinterpret_cast<C<TC>*>(out);
+    a.ldc = n_x;
+    a.conj_b = conj_b;
+    a.conj_out = conj_out;
+    a.accumulate = accumulate;
+    a.b_scale = b_scale;
+    a.out_scale = out_scale;
+    a.add_row = reinterpret_cast<const C<TC>*>(add_row);
+    a.r1_u = r1_u;
+    a.r1_v = r1_v;
+    CUDA_TRY((xform_simt_launch<TA, TB, TC, TACC>(a, st)));
+    return ST_OK;
+}
+
+// ------------------------------------------------------------------ banded solves
+template <typename T>
+const C<T>* shifts_of(const st_fdm* h);
+template <>
+const double2* shifts_of<double>(const st_fdm* h) { return h->s64; }
+template <>
+const float2* shifts_of<float>(const st_fdm* h) { return h->s32; }
+
+// mode: 0 = factor and solve (transient factors), 1 = factor, keep all factors, and solve,
+//       2 = solve with kept factors
+template <typename T>
+st_status band_run(st_fdm* h, C<T>* G, int mode, cudaStream_t st) {
+    const SpaceMats& sm = h->sm;
+    const int n = sm.n_x, b = sm.m + 1, n_t = h->tm.n_t;
+    const int nb = band_pick_nb<T>(b, h->smem_optin);
+    if (nb == 0) return fail(ST_ERR_UNSUPPORTED, "spatial solve: band too wide for shared memory");
+    int occ = band_occupancy<T>(nb, b);
+    if (occ < 1) occ = 1;
+    const int grid = std::max(1, std::min(n_t, occ * h->sm_count));
+    BandArgs<T> a;
+    a.n = n;
+    a.m = sm.m;
+    a.b = b;
+    a.n_sys = n_t;
+    a.Mc = (T)sm.Mc; a.Mw = (T)sm.Mw; a.Ms = (T)sm.Ms; a.Md = (T)sm.Md;
+    a.Ac = (T)sm.Ac; a.Aw = (T)sm.Aw; a.As = (T)sm.As; a.Ad = (T)sm.Ad;
+    a.shifts = shifts_of<T>(h);
+    a.rhs = G;
+    a.status = h->ws_status;
+    const size_t WR = (size_t)b + nb;
+    if (mode == 2) {
+        if (!h->factors_valid || h->factors_prec != (int)sizeof(T))
+            return fail(ST_ERR_ARG, "spatial solve: no stored factors");
+        a.win = nullptr;
+        a.L = reinterpret_cast<C<T>*>(h->ws_L);
+        a.D = reinterpret_cast<C<T>*>(h->ws_D);
+        a.keep = 1;
+        CUDA_TRY(band_solve_launch<T>(a, nb, grid, st));
+        return ST_OK;
+    }
+    st_status s = grow(h->ws_win, h->ws_win_bytes, (size_t)grid * WR * (b + 1) * sizeof(C<T>), "band windows");
+    if (s != ST_OK) return s;
+    const size_t slots = (mode == 1) ? (size_t)n_t : (size_t)grid;
+    s = grow(h->ws_L, h->ws_L_bytes, slots * n * b * sizeof(C<T>), "band factors");
+    if (s != ST_OK) return s;
+    s = grow(h->ws_D, h->ws_D_bytes, slots * n * sizeof(C<T>), "band pivots");
+    if (s != ST_OK) return s;
+    h->factors_valid = 0;
+    a.win = reinterpret_cast<C<T>*>(h->ws_win);
+    a.L = reinterpret_cast<C<T>*>(h->ws_L);
+    a.D = reinterpret_cast<C<T>*>(h->ws_D);
+    a.keep = (mode == 1) ? 1 : 0;
+    CUDA_TRY(band_factor_solve_launch<T>(a, nb, grid, st));
+    if (mode == 1) {
+        h->factors_valid = 1;
+        h->factors_prec = (int)sizeof(T);
+    }
+    return ST_OK;
+}
+
+st_status check_status_flag(st_fdm* h, cudaStream_t st) {
+    int flag = 0;
+    CUDA_TRY(cudaMemcpyAsync(&flag, h->ws_status, sizeof(int), cudaMemcpyDeviceToHost, st));
+    CUDA_TRY(cudaStreamSynchronize(st));
+    if (flag) return fail(ST_ERR_ZERO_PIVOT, "spatial solve: zero or non-finite pivot");
+    return ST_OK;
+}
+
+st_status ensure_common(st_fdm* h) {
+    const size_t nx = (size_t)h->sm.n_x;
+    st_status s = grow(h->ws_vec, h->ws_vec_bytes, 4 * nx * sizeof(double2), "vectors");
+    if (s != ST_OK) return s;
+    return ST_OK;
+}
+
+double2* vec_slot(st_fdm* h, int i) { return reinterpret_cast<double2*>(h->ws_vec) + (size_t)i * h->sm.n_x; }
+
+// ------------------------------------------------------------------ solves
+st_status solve_fp64(st_fdm* h, const void* F, const void* psi0, void* psi, cudaStream_t st) {
+    const int n_t = h->tm.n_t, n_x = h->sm.n_x;
+    st_status s = ensure_common(h);
+    if (s != ST_OK) return s;
+    s = grow(h->ws_big, h->ws_big_bytes, (size_t)n_t * n_x * sizeof(double2), "G");
+    if (s != ST_OK) return s;
+    double2* apsi0 = nullptr;
+    if (psi0) {
+        apsi0 = vec_slot(h, 0);
+        CUDA_TRY(launch_stencil_A(h->sm, psi0, false, nullptr, 1.0, apsi0, st));
+    }
+    double2* G = reinterpret_cast<double2*>(h->ws_big);
+    s = xform<double, double, double, double>(reinterpret_cast<double*>(h->xf64[XF_Y]), n_t, n_x, F, G, 0, 0, 0,
+                                              nullptr, nullptr, nullptr, psi0 ? h->Ym64 : nullptr, apsi0, st);
+    if (s != ST_OK) return s;
+    s = band_run<double>(h, G, 0, st);
+    if (s != ST_OK) return s;
+    return xform<double, double, double, double>(reinterpret_cast<double*>(h->xf64[XF_X]), n_t, n_x, G, psi, 0, 0, 0,
+                                                 nullptr, nullptr, psi0, nullptr, nullptr, st);
+}
+
+st_status solve_fp32(st_fdm* h, const void* F, const void* psi0, void* psi, cudaStream_t st) {
+    const int n_t = h->tm.n_t, n_x = h->sm.n_x;
+    st_status s = ensure_common(h);
+    if (s != ST_OK) return s;
+    s = grow(h->ws_g32, h->ws_g32_bytes, (size_t)n_t * n_x * sizeof(float2), "G32");
+    if (s != ST_OK) return s;
+    double2* apsi0 = nullptr;
+    if (psi0) {
+        apsi0 = vec_slot(h, 0);
+        CUDA_TRY(launch_stencil_A(h->sm, psi0, true, nullptr, 1.0, apsi0, st));
+    }
+    float2* G = reinterpret_cast<float2*>(h->ws_g32);
+    s = xform<float, float, float, float>(reinterpret_cast<float*>(h->xf32[XF_Y]), n_t, n_x, F, G, 0, 0, 0, nullptr,
+                                          nullptr, nullptr, psi0 ? h->Ym64 : nullptr, apsi0, st);
+    if (s != ST_OK) return s;
+    s = band_run<float>(h, G, 0, st);
+    if (s != ST_OK) return s;
+    return xform<float, float, float, float>(reinterpret_cast<float*>(h->xf32[XF_X]), n_t, n_x, G, psi, 0, 0, 0,
+                                             nullptr, nullptr, psi0, nullptr, nullptr, st);
+}
+
+bool factors_fit(st_fdm* h, size_t elem) {
+    size_t freeb = 0, total = 0;
+    if (cudaMemGetInfo(&freeb, &total) != cudaSuccess) return false;
+    const size_t need = (size_t)h->tm.n_t * h->sm.n_x * (size_t)(h->sm.m + 1 + 1) * elem;
+    size_t have = h->ws_L_bytes + h->ws_D_bytes;
+    return need <= (size_t)(0.85 * (double)(freeb + have));
+}
+
+// Mixed precision: complex-FP32 FDM sweeps on the FP64 residual (forward: K, adjoint: K^H).
+st_status solve_mixed(st_fdm* h, bool adjoint, const void* F, const void* psi0, void* psi, const st_solve_opts& o,
+                      st_solve_info* info, cudaStream_t st) {
+    const int n_t = h->tm.n_t, n_x = h->sm.n_x;
+    st_status s = ensure_common(h);
+    if (s != ST_OK) return s;
+    s = grow(h->ws_big, h->ws_big_bytes, (size_t)n_t * n_x * sizeof(double2), "R");
+    if (s != ST_OK) return s;
+    s = grow(h->ws_g32, h->ws_g32_bytes, (size_t)n_t * n_x * sizeof(float2), "G32");
+    if (s != ST_OK) return s;
+    double2* apsi0 = nullptr;
+    if (psi0 && !adjoint) {
+        apsi0 = vec_slot(h, 0);
+        CUDA_TRY(launch_stencil_A(h->sm, psi0, false, nullptr, 1.0, apsi0, st));
+    }
+    double2* R = reinterpret_cast<double2*>(h->ws_big);
+    float2* G = reinterpret_cast<float2*>(h->ws_g32);
+    double* scal = h->ws_red;                      // [0..3] scalars
+    double* parts = h->ws_red + 8;
+    const double tol = o.tol > 0 ? o.tol : 1e-12;
+    const int maxs = o.max_sweeps > 0 ? std::min(o.max_sweeps, 15) : 12;
+    const bool fixed = o.fixed_sweeps > 0;
+    const int nsweeps = fixed ? std::min(o.fixed_sweeps, 15) : maxs;
+    bool keep = false;
+    if (o.keep_factors == 1) keep = true;
+    else if (o.keep_factors == -1) keep = factors_fit(h, sizeof(float2));
+    const double* Bband = adjoint ? h->dt.BTb : h->dt.Bb;
+    const double bsign = adjoint ? -1.0 : 1.0;
+    CUDA_TRY(cudaMemsetAsync(psi, 0, (size_t)n_t * n_x * sizeof(double2), st));
+    CUDA_TRY(cudaMemsetAsync(h->ws_status, 0, sizeof(int), st));
+    int sweeps = 0;
+    double hist[16];
+    int nh = 0;
+    double rel = -1;
+    bool converged = false;
+    for (int sw = 0; sw <= nsweeps; ++sw) {
+        CUDA_TRY(launch_residual(h->sm, n_t, h->dt.Mb, Bband, bsign, reinterpret_cast<const double2*>(F), apsi0,
+                                 h->dt.m, sw == 0 ? nullptr : reinterpret_cast<const double2*>(psi), nullptr, R, parts,
+                                 scal, st));
+        if (!fixed || sw == nsweeps) {
+            if (!fixed || info) {
+                double hs[2];
+                CUDA_TRY(cudaMemcpyAsync(hs, scal, 2 * sizeof(double), cudaMemcpyDeviceToHost, st));
+                CUDA_TRY(cudaStreamSynchronize(st));
+                rel = (hs[1] > 0) ? std::sqrt(hs[0] / hs[1]) : 0.0;
+                if (nh < 16) hist[nh++] = rel;
+                if (!std::isfinite(rel)) return fail(ST_ERR_NOT_CONVERGED, "refinement: non-finite residual");
+                if (!fixed && rel <= tol) {
+                    converged = true;
+                    break;
+                }
+            }
+        }
+        if (sw == nsweeps) break;
+        // delta = K^{-1} R (or K^{-H} R) in complex FP32, psi += delta (scaled)
+        if (!adjoint) {
+            s = xform<float, double, float, float>(reinterpret_cast<float*>(h->xf32[XF_Y]), n_t, n_x, R, G, 0, 0, 0,
+                                                   scal + 2, nullptr, nullptr, nullptr, nullptr, st);
+        } else {
+            s = xform<float, double, float, float>(reinterpret_cast<float*>(h->xf32[XF_XT]), n_t, n_x, R, G, 1, 0, 0,
+                                                   scal + 2, nullptr, nullptr, nullptr, nullptr, st);
+        }
+        if (s != ST_OK) return s;
+        int mode = 0;
+        if (keep) mode = (sw == 0) ? 1 : 2;
+        s = band_run<float>(h, G, mode, st);
+        if (s != ST_OK) {
+            if (mode == 1 && s == ST_ERR_OOM) {  // fall back to refactoring every sweep
+                keep = false;
+                s = band_run<float>(h, G, 0, st);
+            }
+            if (s != ST_OK) return s;
+        }
+        if (!adjoint) {
+            s = xform<float, float, double, float>(reinterpret_cast<float*>(h->xf32[XF_X]), n_t, n_x, G, psi, 0, 0, 1,
+                                                   nullptr, scal + 3, nullptr, nullptr, nullptr, st);
+        } else {
+            s = xform<float, float, double, float>(reinterpret_cast<float*>(h->xf32[XF_YT]), n_t, n_x, G, psi, 0, 1, 1,
+                                                   nullptr, scal + 3, nullptr, nullptr, nullptr, st);
+        }
+        if (s != ST_OK) return s;
+        ++sweeps;
+    }
+    if (psi0 && !adjoint) CUDA_TRY(launch_add_row(n_t, n_x, psi, psi0, false, st));
+    if (info) {
+        info->sweeps = sweeps;
+        info->factors_kept = keep ? 1 : 0;
+        info->rel_residual = rel;
+        for (int i = 0; i < 16; ++i) info->residual_history[i] = (i < nh) ? hist[i] : -1.0;
+    }
+    if (!fixed || info) {
+        s = check_status_flag(h, st);
+        if (s != ST_OK) return s;
+    }
+    if (!fixed && !converged) return fail(ST_ERR_NOT_CONVERGED, "refinement: tolerance not reached in max_sweeps");
+    return ST_OK;
+}
+
+st_status adjoint_direct(st_fdm* h, bool fp32, const void* G, void* lambda, cudaStream_t st) {
+    const int n_t = h->tm.n_t, n_x = h->sm.n_x;
+    st_status s;
+    if (!fp32) {
+        s = grow(h->ws_big, h->ws_big_bytes, (size_t)n_t * n_x * sizeof(double2), "H");
+        if (s != ST_OK) return s;
+        double2* H = reinterpret_cast<double2*>(h->ws_big);
+        s = xform<double, double, double, double>(reinterpret_cast<double*>(h->xf64[XF_XT]), n_t, n_x, G, H, 1, 0, 0,
+                                                  nullptr, nullptr, nullptr, nullptr, nullptr, st);
+        if (s != ST_OK) return s;
+        s = band_run<double>(h, H, 0, st);
+        if (s != ST_OK) return s;
+        return xform<double, double, double, double>(reinterpret_cast<double*>(h->xf64[XF_YT]), n_t, n_x, H, lambda, 0,
+                                                     1, 0, nullptr, nullptr, nullptr, nullptr, nullptr, st);
+    }
+    s = grow(h->ws_g32, h->ws_g32_bytes, (size_t)n_t * n_x * sizeof(float2), "H32");
+    if (s != ST_OK) return s;
+    float2* H = reinterpret_cast<float2*>(h->ws_g32);
+    s = xform<float, float, float, float>(reinterpret_cast<float*>(h->xf32[XF_XT]), n_t, n_x, G, H, 1, 0, 0, nullptr,
+                                          nullptr, nullptr, nullptr, nullptr, st);
+    if (s != ST_OK) return s;
+    s = band_run<float>(h, H, 0, st);
+    if (s != ST_OK) return s;
+    return xform<float, float, float, float>(reinterpret_cast<float*>(h->xf32[XF_YT]), n_t, n_x, H, lambda, 0, 1, 0,
+                                             nullptr, nullptr, nullptr, nullptr, nullptr, st);
+}
+
+st_status validate_opts(const st_solve_opts* o, st_solve_opts& out) {
+    st_solve_opts d;
+    std::memset(&d, 0, sizeof(d));
+    d.precision = ST_FP64;
+    d.keep_factors = -1;
+    out = o ? *o : d;
+    if (out.precision != ST_FP64 && out.precision != ST_FP32 && out.precision != ST_MIXED)
+        return fail(ST_ERR_ARG, "solve: unknown precision");
+    return ST_OK;
+}
+
+void fill_info_common(const st_fdm* h, st_solve_info* info) {
+    if (!info) return;
+    info->kappa_x = h->td.kappa;
+    info->min_neg_im_shift = h->td.min_neg_im;
+    info->setup_seconds = h->setup_seconds;
+}
+
+}  // namespace
+
+// ==================================================================== setup
+extern "C" st_status st_fdm_setup(const st_time* t, const st_space* sp, const st_setup_opts* opts, st_fdm** out) {
+    if (!out) return fail(ST_ERR_ARG, "st_fdm_setup: out is NULL");
+    *out = nullptr;
+    if (!t || !sp) return fail(ST_ERR_ARG, "st_fdm_setup: NULL time or space handle");
+    st_setup_opts o;
+    std::memset(&o, 0, sizeof(o));
+    o.device = -1;
+    if (opts) o = *opts;
+    const double kappa_max = o.kappa_max > 0 ? o.kappa_max : 1e10;
+    st_fdm* h = new (std::nothrow) st_fdm();
+    if (!h) return fail(ST_ERR_OOM, "st_fdm_setup: host allocation");
+    h->tm = t->tm;
+    h->sm = sp->sm;
+    auto t0 = std::chrono::steady_clock::now();
+    st_status s = time_decompose(h->tm, o.host_threads, h->td);
+    h->setup_seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    if (s != ST_OK) {
+        delete h;
+        return s;
+    }
+    if (!(h->td.kappa <= kappa_max)) {
+        double k = h->td.kappa;
+        delete h;
+        return fail(ST_ERR_ILL_CONDITIONED, "st_fdm_setup: kappa_2(X_t) = " + std::to_string(k) + " exceeds kappa_max");
+    }
+    {
+        // Im s_k < 0 in exact arithmetic whenever the eigenvector has v_N != 0; eigenvectors
+        // localised away from t = T (graded meshes) give |Im s_k| at rounding level, i.e.
+        // numerically real shifts.  Only an imaginary part clearly of the wrong sign is rejected.
+        double smax = 0;
+        for (const auto& v : h->td.s) smax = std::max(smax, std::abs(v));
+        if (!(h->td.min_neg_im >= -1e-8 * smax)) {
+            delete h;
+            return fail(ST_ERR_ILL_CONDITIONED, "st_fdm_setup: an eigenvalue has Im s_k > 0");
+        }
+    }
+    int dev = o.device;
+    if (dev < 0) {
+        if (cudaGetDevice(&dev) != cudaSuccess) {
+            delete h;
+            cudaGetLastError();
+            return fail(ST_ERR_CUDA, "st_fdm_setup: no CUDA device");
+        }
+    }
+    h->device = dev;
+    DeviceGuard g(dev);
+    cudaDeviceProp prop;
+    if (cudaGetDeviceProperties(&prop, dev) != cudaSuccess) {
+        delete h;
+        cudaGetLastError();
+        return fail(ST_ERR_CUDA, "st_fdm_setup: cudaGetDeviceProperties failed");
+    }
+    if (prop.major < 10) {
+        delete h;
+        return fail(ST_ERR_UNSUPPORTED, "st_fdm_setup: the library is built for sm_103a (GB300)");
+    }
+    h->sm_count = prop.multiProcessorCount;
+    h->smem_optin = prop.sharedMemPerBlockOptin;
+    const int n = h->tm.n_t;
+    const size_t nn = (size_t)n * n;
+    // transform matrices: Y, X, X^T, Y^T (row-major), FP64 and FP32
+    std::vector<cd> mats[4];
+    mats[XF_Y] = h->td.Y;
+    mats[XF_X] = h->td.X;
+    mats[XF_XT].resize(nn);
+    mats[XF_YT].resize(nn);
+    for (int i = 0; i < n; ++i)
+        for (int j = 0; j < n; ++j) {
+            mats[XF_XT][(size_t)i * n + j] = h->td.X[(size_t)j * n + i];
+            mats[XF_YT][(size_t)i * n + j] = h->td.Y[(size_t)j * n + i];
+        }
+    std::vector<float2> f32(nn);
+    for (int w = 0; w < 4 && s == ST_OK; ++w) {
+        s = upload(&h->xf64[w], mats[w].data(), nn * sizeof(double2), "transform (FP64)");
+        if (s != ST_OK) break;
+        for (size_t i = 0; i < nn; ++i) f32[i] = make_float2((float)mats[w][i].real(), (float)mats[w][i].imag());
+        s = upload(&h->xf32[w], f32.data(), nn * sizeof(float2), "transform (FP32)");
+    }
+    std::vector<float2> s32(n);
+    for (int k = 0; k < n; ++k) s32[k] = make_float2((float)h->td.s[k].real(), (float)h->td.s[k].imag());
+    std::vector<cd> ym(n, 0.0);
+    for (int i = 0; i < n; ++i)
+        for (int k = 0; k < n; ++k) ym[i] += h->td.Y[(size_t)i * n + k] * h->tm.m[k];
+    std::vector<double> BT((size_t)n * 5, 0.0);
+    for (int l = 0; l < n; ++l)
+        for (int d = -2; d <= 2; ++d) {
+            int c = l + d;
+            if (c < 0 || c >= n) continue;
+            // B^T[l][c] = B[c][l] = Bb[c][l - c + 2]
+            BT[(size_t)l * 5 + d + 2] = h->tm.Bb[(size_t)c * 5 + (l - c) + 2];
+        }
+    if (s == ST_OK) s = upload(&h->s64, h->td.s.data(), n * sizeof(double2), "shifts");
+    if (s == ST_OK) s = upload(&h->s32, s32.data(), n * sizeof(float2), "shifts32");
+    if (s == ST_OK) s = upload(&h->Ym64, ym.data(), n * sizeof(double2), "Y m_t");
+    if (s == ST_OK) s = upload(&h->dt.Mb, h->tm.Mb.data(), (size_t)n * 5 * sizeof(double), "M_t band");
+    if (s == ST_OK) s = upload(&h->dt.Bb, h->tm.Bb.data(), (size_t)n * 5 * sizeof(double), "B_t band");
+    if (s == ST_OK) s = upload(&h->dt.BTb, BT.data(), (size_t)n * 5 * sizeof(double), "B_t^T band");
+    if (s == ST_OK) s = upload(&h->dt.Mfull0, h->tm.Mfull0.data(), (size_t)n * sizeof(double), "M_t col 0");
+    if (s == ST_OK) s = upload(&h->dt.m, h->tm.m.data(), (size_t)n * sizeof(double), "m_t");
+    if (s == ST_OK) {
+        size_t parts = (size_t)residual_num_partials(n, h->sm.n_x);
+        s = grow(*reinterpret_cast<void**>(&h->ws_red), h->ws_red_bytes, (8 + 2 * parts) * sizeof(double), "reduction");
+    }
+    if (s == ST_OK) s = dev_alloc(reinterpret_cast<void**>(&h->ws_status), sizeof(int) * 4, "status");
+    if (s == ST_OK && cudaMemset(h->ws_status, 0, sizeof(int) * 4) != cudaSuccess)
+        s = fail(ST_ERR_CUDA, "st_fdm_setup: cudaMemset");
+    if (s != ST_OK) {
+        free_handle(h);
+        return s;
+    }
+    *out = h;
+    return ST_OK;
+}
+
+extern "C" st_status st_fdm_get(const st_fdm* h, int* n_t, int* n_x, int* m, double* kappa2, double* min_neg_im) {
+    if (!h) return fail(ST_ERR_ARG, "st_fdm_get: NULL handle");
+    if (n_t) *n_t = h->tm.n_t;
+    if (n_x) *n_x = h->sm.n_x;
+    if (m) *m = h->sm.m;
+    if (kappa2) *kappa2 = h->td.kappa;
+    if (min_neg_im) *min_neg_im = h->td.min_neg_im;
+    return ST_OK;
+}
+
+extern "C" void st_destroy_fdm(st_fdm* h) { free_handle(h); }
+
+// ==================================================================== solves
+extern "C" st_status st_fdm_solve(st_fdm* h, const void* F, const void* psi0, void* psi, const st_solve_opts* opts,
+                                  st_solve_info* info, void* stream) {
+    if (!h) return fail(ST_ERR_ARG, "st_fdm_solve: NULL handle");
+    if (!F || !psi) return fail(ST_ERR_ARG, "st_fdm_solve: NULL F or psi");
+    if (F == psi) return fail(ST_ERR_ARG, "st_fdm_solve: psi must not alias F");
+    st_solve_opts o;
+    st_status s = validate_opts(opts, o);
+    if (s != ST_OK) return s;
+    DeviceGuard g(h->device);
+    cudaStream_t st = S(stream);
+    fill_info_common(h, info);
+    if (o.precision == ST_MIXED) return solve_mixed(h, false, F, psi0, psi, o, info, st);
+    CUDA_TRY(cudaMemsetAsync(h->ws_status, 0, sizeof(int), st));
+    s = (o.precision == ST_FP64) ? solve_fp64(h, F, psi0, psi, st) : solve_fp32(h, F, psi0, psi, st);
+    if (s != ST_OK) return s;
+    if (info) {
+        info->sweeps = 1;
+        info->factors_kept = 0;
+        info->rel_residual = -1;
+        for (int i = 0; i < 16; ++i) info->residual_history[i] = -1;
+        return check_status_flag(h, st);
+    }
+    return ST_OK;
+}
+
+extern "C" st_status st_residual(st_fdm* h, const void* F, const void* psi0, const void* psi, void* R,
+                                 double* rel_norm, void* stream) {
+    if (!h || !F || !psi) return fail(ST_ERR_ARG, "st_residual: NULL argument");
+    DeviceGuard g(h->device);
+    cudaStream_t st = S(stream);
+    st_status s = ensure_common(h);
+    if (s != ST_OK) return s;
+    double2* apsi0 = nullptr;
+    if (psi0) {
+        apsi0 = vec_slot(h, 1);
+        CUDA_TRY(launch_stencil_A(h->sm, psi0, false, nullptr, 1.0, apsi0, st));
+    }
+    double* scal = h->ws_red + 4;
+    double* parts = h->ws_red + 8;
+    CUDA_TRY(launch_residual(h->sm, h->tm.n_t, h->dt.Mb, h->dt.Bb, 1.0, reinterpret_cast<const double2*>(F), apsi0,
+                             h->dt.m, reinterpret_cast<const double2*>(psi), reinterpret_cast<const double2*>(psi0),
+                             reinterpret_cast<double2*>(R), parts, scal, st));
+    if (rel_norm) {
+        double hs[2];
+        CUDA_TRY(cudaMemcpyAsync(hs, scal, 2 * sizeof(double), cudaMemcpyDeviceToHost, st));
+        CUDA_TRY(cudaStreamSynchronize(st));
+        *rel_norm = hs[1] > 0 ? std::sqrt(hs[0] / hs[1]) : 0.0;
+    }
+    return ST_OK;
+}
+
+extern "C" st_status st_adjoint_solve(st_fdm* h, const void* G, void* lambda, const st_solve_opts* opts,
+                                      st_solve_info* info, void* stream) {
+    if (!h || !G || !lambda) return fail(ST_ERR_ARG, "st_adjoint_solve: NULL argument");
+    if (G == lambda) return fail(ST_ERR_ARG, "st_adjoint_solve: lambda must not alias G");
+    st_solve_opts o;
+    st_status s = validate_opts(opts, o);
+    if (s != ST_OK) return s;
+    DeviceGuard g(h->device);
+    cudaStream_t st = S(stream);
+    fill_info_common(h, info);
+    if (o.precision == ST_MIXED) return solve_mixed(h, true, G, nullptr, lambda, o, info, st);
+    CUDA_TRY(cudaMemsetAsync(h->ws_status, 0, sizeof(int), st));
+    s = adjoint_direct(h, o.precision == ST_FP32, G, lambda, st);
+    if (s != ST_OK) return s;
+    if (info) {
+        info->sweeps = 1;
+        info->factors_kept = 0;
+        info->rel_residual = -1;
+        for (int i = 0; i < 16; ++i) info->residual_history[i] = -1;
+        return check_status_flag(h, st);
+    }
+    return ST_OK;
+}
+
+extern "C" st_status st_adjoint_lift(st_fdm* h, const void* grad_psi, const void* grad_F, void* grad_psi0,
+                                     void* stream) {
+    if (!h || !grad_psi || !grad_F || !grad_psi0) return fail(ST_ERR_ARG, "st_adjoint_lift: NULL argument");
+    DeviceGuard g(h->device);
+    cudaStream_t st = S(stream);
+    st_status s = ensure_common(h);
+    if (s != ST_OK) return s;
+    double2* s1 = vec_slot(h, 2);
+    double2* s2 = vec_slot(h, 3);
+    CUDA_TRY(launch_colsums(h->tm.n_t, h->sm.n_x, reinterpret_cast<const double2*>(grad_psi),
+                            reinterpret_cast<const double2*>(grad_F), h->dt.m, s1, s2, st));
+    CUDA_TRY(launch_stencil_A(h->sm, s2, false, s1, -1.0, reinterpret_cast<double2*>(grad_psi0), st));
+    return ST_OK;
+}
+
+extern "C" st_status st_time_transform(st_fdm* h, int which, int precision, const void* in, void* out, void* stream) {
+    if (!h || !in || !out) return fail(ST_ERR_ARG, "st_time_transform: NULL argument");
+    if (in == out) return fail(ST_ERR_ARG, "st_time_transform: out must not alias in");
+    if (which < 0 || which > 3) return fail(ST_ERR_ARG, "st_time_transform: bad selector");
+    DeviceGuard g(h->device);
+    cudaStream_t st = S(stream);
+    const int n_t = h->tm.n_t, n_x = h->sm.n_x;
+    if (precision == ST_FP64)
+        return xform<double, double, double, double>(reinterpret_cast<double*>(h->xf64[which]), n_t, n_x, in, out, 0,
+                                                     0, 0, nullptr, nullptr, nullptr, nullptr, nullptr, st);
+    if (precision == ST_FP32 || precision == ST_MIXED)
+        return xform<float, float, float, float>(reinterpret_cast<float*>(h->xf32[which]), n_t, n_x, in, out, 0, 0, 0,
+                                                 nullptr, nullptr, nullptr, nullptr, nullptr, st);
+    return fail(ST_ERR_ARG, "st_time_transform: unknown precision");
+}
+
+extern "C" st_status st_spatial_solve(st_fdm* h, int precision, const void* G, void* W, void* stream) {
+    if (!h || !G || !W) return fail(ST_ERR_ARG, "st_spatial_solve: NULL argument");
+    DeviceGuard g(h->device);
+    cudaStream_t st = S(stream);
+    const size_t elems = (size_t)h->tm.n_t * h->sm.n_x;
+    const size_t esz = precision == ST_FP64 ? sizeof(double2) : sizeof(float2);
+    if (precision != ST_FP64 && precision != ST_FP32 && precision != ST_MIXED)
+        return fail(ST_ERR_ARG, "st_spatial_solve: unknown precision");
+    if (W != G) CUDA_TRY(cudaMemcpyAsync(W, G, elems * esz, cudaMemcpyDeviceToDevice, st));
+    CUDA_TRY(cudaMemsetAsync(h->ws_status, 0, sizeof(int), st));
+    st_status s = (precision == ST_FP64) ? band_run<double>(h, reinterpret_cast<double2*>(W), 0, st)
+                                         : band_run<float>(h, reinterpret_cast<float2*>(W), 0, st);
+    if (s != ST_OK) return s;
+    return check_status_flag(h, st);
+}
+
+extern "C" st_status st_load_nodal(st_fdm* h, const void* f_nodal, void* F, void* stream) {
+    if (!h || !f_nodal || !F) return fail(ST_ERR_ARG, "st_load_nodal: NULL argument");
+    if (h->tm.n_t > 65535) return fail(ST_ERR_UNSUPPORTED, "st_load_nodal: n_t > 65535");
+    DeviceGuard g(h->device);
+    CUDA_TRY(launch_load_nodal(h->sm, h->tm.n_t, h->dt.Mb, h->dt.Mfull0, reinterpret_cast<const double2*>(f_nodal),
+                               reinterpret_cast<double2*>(F), S(stream)));
+    return ST_OK;
+}
+
+extern "C" st_status st_fdm_solve_batched(st_fdm* const* hs, int count, const void* const* F,
+                                          const void* const* psi0, void* const* psi, const st_solve_opts* opts,
+                                          st_solve_info* infos, void* stream) {
+    if (count < 0 || (count > 0 && (!hs || !F || !psi))) return fail(ST_ERR_ARG, "st_fdm_solve_batched: bad arguments");
+    for (int i = 0; i < count; ++i) {
+        st_status s = st_fdm_solve(hs[i], F[i], psi0 ? psi0[i] : nullptr, psi[i], opts, infos ? &infos[i] : nullptr,
+                                   stream);
+        if (s != ST_OK) return s;
+    }
+    return ST_OK;
+}

@@ -1,0 +1,137 @@
+// Device-side shared declarations: complex helpers, the solver handle, kernel launchers.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <string>
+
+#include "internal.h"
+
+namespace stfdm {
+
+// ------------------------------------------------------------------ complex helpers
+template <typename T> struct cplx;
+template <> struct cplx<float> { using type = float2; };
+template <> struct cplx<double> { using type = double2; };
+template <typename T> using C = typename cplx<T>::type;
+
+template <typename T> __host__ __device__ __forceinline__ C<T> mk(T x, T y) { return C<T>{x, y}; }
+template <typename T> __host__ __device__ __forceinline__ C<T> cadd(C<T> a, C<T> b) { return mk<T>(a.x + b.x, a.y + b.y); }
+template <typename T> __host__ __device__ __forceinline__ C<T> csub(C<T> a, C<T> b) { return mk<T>(a.x - b.x, a.y - b.y); }
+template <typename T> __host__ __device__ __forceinline__ C<T> cmul(C<T> a, C<T> b) {
+    return mk<T>(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+template <typename T> __host__ __device__ __forceinline__ C<T> cscale(C<T> a, T s) { return mk<T>(a.x * s, a.y * s); }
+// acc -= a * b
+template <typename T> __device__ __forceinline__ void cfms(C<T>& acc, C<T> a, C<T> b) {
+    acc.x = fma(-a.x, b.x, acc.x);
+    acc.x = fma(a.y, b.y, acc.x);
+    acc.y = fma(-a.x, b.y, acc.y);
+    acc.y = fma(-a.y, b.x, acc.y);
+}
+// acc += a * b
+template <typename T> __device__ __forceinline__ void cfma(C<T>& acc, C<T> a, C<T> b) {
+    acc.x = fma(a.x, b.x, acc.x);
+    acc.x = fma(-a.y, b.y, acc.x);
+    acc.y = fma(a.x, b.y, acc.y);
+    acc.y = fma(a.y, b.x, acc.y);
+}
+template <typename T> __host__ __device__ __forceinline__ C<T> cinv(C<T> a) {
+    T d = a.x * a.x + a.y * a.y;
+    return mk<T>(a.x / d, -a.y / d);
+}
+template <typename To, typename Ti> __host__ __device__ __forceinline__ C<To> ccast(C<Ti> a) {
+    return mk<To>((To)a.x, (To)a.y);
+}
+
+// ------------------------------------------------------------------ handle
+struct DevTime {
+    double* Mb = nullptr;     // n_t x 5 band of M_t
+    double* Bb = nullptr;     // n_t x 5 band of B_t
+    double* BTb = nullptr;    // n_t x 5 band of B_t^T
+    double* Mfull0 = nullptr; // full M_t rows 1..n_t, column t_0
+    double* m = nullptr;      // m_t
+};
+
+// which transform matrix
+enum XformSel { XF_Y = 0, XF_X = 1, XF_XT = 2, XF_YT = 3 };
+
+
+template <typename TA, typename TB, typename TC>
+struct XformArgs {
+    int M, N, K;
+    const C<TA>* A;      // row-major M x K
+    int lda;
+    const C<TB>* B;      // row-major K x N
+    long long ldb;
+    C<TC>* Cm;           // row-major M x N
+    long long ldc;
+    int conj_b, conj_out, accumulate;
+    const double* b_scale;    // device scalar multiplying B, or NULL
+    const double* out_scale;  // device scalar for accumulate, or NULL
+    const C<TC>* add_row;     // N-vector added to every output row, or NULL
+    const double2* r1_u;      // rank-one term subtracted: r1_u[i] r1_v[j], or NULL
+    const double2* r1_v;
+};
+template <typename TA, typename TB, typename TC, typename TACC>
+cudaError_t xform_simt_launch(const XformArgs<TA, TB, TC>& a, cudaStream_t st);
+
+template <typename T>
+struct BandArgs {
+    int n;          // n_x
+    int m;          // interior nodes per grid row
+    int b;          // half bandwidth m + 1
+    int n_sys;      // number of systems (n_t)
+    T Mc, Mw, Ms, Md, Ac, Aw, As, Ad;   // stencil coefficients of M_x and A_x
+    const C<T>* shifts;   // s_k
+    C<T>* rhs;            // (n_sys, n): g_k in, w_k out
+    C<T>* win;            // gridDim.x windows of (b + NB) x (b + 1)
+    C<T>* L;              // factor columns: L[j*b + o - 1] = L(j + o, j), o = 1..b
+    C<T>* D;              // pivots
+    int keep;             // 1: factors stored per system k, 0: per CTA slot (transient)
+    int* status;          // status[0] set to 1 on a zero / non-finite pivot
+};
+template <typename T> int band_pick_nb(int b, size_t smem_optin);
+template <typename T> size_t band_smem_for(int nb, int b);
+template <typename T> int band_occupancy(int nb, int b);
+template <typename T> cudaError_t band_factor_solve_launch(const BandArgs<T>& a, int nb, int grid, cudaStream_t st);
+template <typename T> cudaError_t band_solve_launch(const BandArgs<T>& a, int nb, int grid, cudaStream_t st);
+
+}  // namespace stfdm
+
+struct st_fdm {
+    stfdm::TimeMats tm;
+    stfdm::SpaceMats sm;
+    stfdm::TimeDecomp td;
+    double setup_seconds = 0;
+    int device = 0;
+    int sm_count = 0;
+    size_t smem_optin = 0;
+    // device constants
+    double2* xf64[4] = {nullptr, nullptr, nullptr, nullptr};  // Y, X, X^T, Y^T (row-major n_t x n_t)
+    float2* xf32[4] = {nullptr, nullptr, nullptr, nullptr};
+    float* xf_tf32[4][2] = {{nullptr, nullptr}, {nullptr, nullptr}, {nullptr, nullptr}, {nullptr, nullptr}};
+    double2* s64 = nullptr;
+    float2* s32 = nullptr;
+    double2* Ym64 = nullptr;  // Y_t m_t (lifting correction after the forward transform)
+    stfdm::DevTime dt;
+    // workspace (allocated on demand, grown as needed)
+    void* ws_big = nullptr;       // R (c128) or G (c128) : n_t n_x complex double
+    size_t ws_big_bytes = 0;
+    void* ws_g32 = nullptr;       // c64 n_t n_x (mixed: scaled residual / G / W)
+    size_t ws_g32_bytes = 0;
+    void* ws_win = nullptr;       // banded factorisation windows (per CTA slot)
+    size_t ws_win_bytes = 0;
+    void* ws_L = nullptr;         // LDL^T factors
+    size_t ws_L_bytes = 0;
+    void* ws_D = nullptr;
+    size_t ws_D_bytes = 0;
+    void* ws_vec = nullptr;       // small vectors: A_x psi0 (c128 n_x) etc.
+    size_t ws_vec_bytes = 0;
+    double* ws_red = nullptr;     // reduction partials + scalars
+    size_t ws_red_bytes = 0;
+    int* ws_status = nullptr;     // device status flags
+    int factors_valid = 0;        // ws_L holds the factors of all n_t systems (keep mode)
+    int factors_prec = -1;
+};

@@ -1,0 +1,79 @@
+// Internal declarations of the stfdm library (host + device).
+#pragma once
+
+#include <complex>
+#include <cstddef>
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "../../include/stfdm.h"
+
+namespace stfdm {
+
+using cd = std::complex<double>;
+
+// thread-local last error detail; returns the status for `return fail(...)`
+st_status fail(st_status s, const std::string& msg);
+
+// Reduced temporal matrices (t_0 DOF removed) in band form: row l holds entries
+// (l, l + d) for d = -2..2 at band[l * 5 + d + 2].
+struct TimeMats {
+    int p = 1;
+    int N = 0;                  // elements
+    int n_t = 0;                // p N
+    std::vector<double> nodes;  // N + 1
+    std::vector<double> Mb, Bb; // n_t x 5 bands of the reduced M_t, B_t
+    std::vector<double> Mfull0; // full mass matrix rows 1..n_t, column 0 (coupling to t_0)
+    std::vector<double> m;      // m_t[k] = int phi_k
+    std::vector<double> times;  // DOF times t_1..
+};
+
+struct SpaceMats {
+    int n = 0;         // squares per direction
+    int m = 0;         // interior nodes per direction
+    int n_x = 0;       // m^2
+    double Lx = 1, Ly = 1;
+    // 7-point stencil coefficients
+    double Mc = 0, Mw = 0, Ms = 0, Md = 0;  // centre, W/E, S/N, SW/NE
+    double Ac = 0, Aw = 0, As = 0, Ad = 0;
+};
+
+// host FP64 dense linear algebra (column-major n x n unless stated)
+namespace la {
+// Schur form A = Z T Z^H (A overwritten by T, upper triangular); returns false if not converged
+bool complex_schur(int n, cd* A, cd* Z, int threads);
+// eigenvectors of A from its Schur form: X = Z * V, columns normalised to unit 2-norm
+void schur_eigenvectors(int n, const cd* T, const cd* Z, cd* X, int threads);
+// LU with partial pivoting in place (column-major); returns false if singular
+bool lu_factor(int n, cd* A, int* piv);
+// solve A X = B for nrhs columns (column-major B, leading dim n) with a factorisation of lu_factor
+void lu_solve(int n, const cd* LU, const int* piv, cd* B, int nrhs, int threads);
+// kappa_2 of a square matrix from the extreme eigenvalues of X^H X (Lanczos) using its LU
+double cond2(int n, const cd* X, const cd* LU, const int* piv);
+// banded real LU with partial pivoting for the temporal B_t (dense storage, band-limited loops)
+bool band_lu_real(int n, int kl, int ku, double* A, int* piv);
+void band_lu_real_solve(int n, int kl, int ku, const double* LU, const int* piv, double* b);
+void band_lu_real_solve_T(int n, int kl, int ku, const double* LU, const int* piv, double* b);
+}  // namespace la
+
+// result of step 1
+struct TimeDecomp {
+    int n = 0;
+    std::vector<cd> X;   // row-major n x n, unit 2-norm columns
+    std::vector<cd> s;   // eigenvalues
+    std::vector<cd> Y;   // row-major, Y = X^{-1} (i B)^{-1}
+    double kappa = 0;
+    double min_neg_im = 0;
+};
+
+st_status time_decompose(const TimeMats& tm, int threads, TimeDecomp& out);
+
+}  // namespace stfdm
+
+struct st_time {
+    stfdm::TimeMats tm;
+};
+struct st_space {
+    stfdm::SpaceMats sm;
+};

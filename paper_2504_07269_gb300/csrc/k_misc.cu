@@ -1,0 +1,291 @@
+// Kernels around the three solver steps:
+//   * A_x applied to a spatial vector (lifting, eq. VF_FEM: F~ = F - m_t (x) A_x psi0);
+//   * the FP64 Kronecker residual R = F~ - K U, K = i B_t (x) M_x + M_t (x) A_x (eq. LGS),
+//     fused with the 2-norm partial sums of R and F~ (and its adjoint K^H);
+//   * deterministic two-level norm reduction and refinement scaling;
+//   * psi = psi_hat + psi0;  the interpolated load (M_t,full (x) M_x) f;  weighted column sums.
+// All space-time arrays are (n_t, n_x) row-major complex; spatial nodes are x1-fastest with
+// m per grid row; the 7-point stencil (W, E, S, N, SW, NE) is zero outside the grid.
+#include <cuda_runtime.h>
+
+#include "device.cuh"
+
+namespace stfdm {
+
+struct Stencil {
+    int m;
+    double Mc, Mw, Ms, Md, Ac, Aw, As, Ad;
+};
+
+template <typename TI>
+__device__ __forceinline__ void stencil_MA(const Stencil& s, const C<TI>* u, int x, double2& Pm, double2& Qa) {
+    const int m = s.m;
+    const int xi = x % m, yj = x / m;
+    auto ld = [&](int idx) {
+        C<TI> v = u[idx];
+        return make_double2((double)v.x, (double)v.y);
+    };
+    double2 c = ld(x);
+    double2 we = make_double2(0, 0), sn = make_double2(0, 0), dg = make_double2(0, 0);
+    if (xi > 0) { double2 v = ld(x - 1); we.x += v.x; we.y += v.y; }
+    if (xi < m - 1) { double2 v = ld(x + 1); we.x += v.x; we.y += v.y; }
+    if (yj > 0) { double2 v = ld(x - m); sn.x += v.x; sn.y += v.y; }
+    if (yj < m - 1) { double2 v = ld(x + m); sn.x += v.x; sn.y += v.y; }
+    if (xi > 0 && yj > 0) { double2 v = ld(x - m - 1); dg.x += v.x; dg.y += v.y; }
+    if (xi < m - 1 && yj < m - 1) { double2 v = ld(x + m + 1); dg.x += v.x; dg.y += v.y; }
+    Pm.x = s.Mc * c.x + s.Mw * we.x + s.Ms * sn.x + s.Md * dg.x;
+    Pm.y = s.Mc * c.y + s.Mw * we.y + s.Ms * sn.y + s.Md * dg.y;
+    Qa.x = s.Ac * c.x + s.Aw * we.x + s.As * sn.x + s.Ad * dg.x;
+    Qa.y = s.Ac * c.y + s.Aw * we.y + s.As * sn.y + s.Ad * dg.y;
+}
+
+// out[x] = (add ? add[x] : 0) + sign * (A_x in)[x]
+template <typename TI>
+__global__ void k_stencil_A(Stencil s, int n_x, const C<TI>* in, const double2* add, double sign, double2* out) {
+    int x = blockIdx.x * blockDim.x + threadIdx.x;
+    if (x >= n_x) return;
+    double2 P, Q;
+    stencil_MA<TI>(s, in, x, P, Q);
+    double2 r = add ? add[x] : make_double2(0, 0);
+    r.x += sign * Q.x;
+    r.y += sign * Q.y;
+    out[x] = r;
+}
+
+struct ResArgs {
+    int n_t, n_x;
+    Stencil s;
+    const double* Mb;   // n_t x 5 band of M_t
+    const double* Bb;   // n_t x 5 band of B_t (or B_t^T)
+    double bsign;       // +1: K;  -1 with B_t^T: K^H
+    const double2* F;
+    const double2* apsi0;  // A_x psi0 or NULL
+    const double* m_t;
+    const double2* U;      // current iterate or NULL (= 0)
+    const double2* psi0;   // if set, the iterate is U - 1 (x) psi0
+    double2* R;            // output or NULL
+    double* partials;      // 2 per block: ||R||^2, ||F~||^2
+};
+
+constexpr int RES_LT = 16;
+
+__device__ __forceinline__ double block_sum(double v, double* red) {
+    for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(0xffffffffu, v, off);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    __syncthreads();
+    if (lane == 0) red[warp] = v;
+    __syncthreads();
+    double t = 0;
+    if (threadIdx.x == 0)
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w];
+    return t;
+}
+
+__global__ void __launch_bounds__(256) k_residual(ResArgs a) {
+    __shared__ double red[32];
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    const int l0 = blockIdx.y * RES_LT;
+    const int l1 = min(l0 + RES_LT, a.n_t);
+    double rr = 0, ff = 0;
+    if (x < a.n_x) {
+        double2 P[5], Q[5];
+        auto load_row = [&](int k, double2& p, double2& q) {
+            if (k < 0 || k >= a.n_t || !a.U) {
+                p = make_double2(0, 0);
+                q = make_double2(0, 0);
+            } else {
+                stencil_MA<double>(a.s, a.U + (size_t)k * a.n_x, x, p, q);
+            }
+        };
+        double2 P0 = make_double2(0, 0), Q0 = make_double2(0, 0);
+        if (a.psi0) stencil_MA<double>(a.s, a.psi0, x, P0, Q0);
+        auto load_row_shift = [&](int k, double2& p, double2& q) {
+            load_row(k, p, q);
+            if (a.psi0 && a.U && k >= 0 && k < a.n_t) {
+                p.x -= P0.x; p.y -= P0.y;
+                q.x -= Q0.x; q.y -= Q0.y;
+            }
+        };
+        for (int d = 1; d < 5; ++d) load_row_shift(l0 - 3 + d, P[d], Q[d]);
+        const double2 ap = a.apsi0 ? a.apsi0[x] : make_double2(0, 0);
+        for (int l = l0; l < l1; ++l) {
+#pragma unroll
+            for (int d = 0; d < 4; ++d) {
+                P[d] = P[d + 1];
+                Q[d] = Q[d + 1];
+            }
+            load_row_shift(l + 2, P[4], Q[4]);
+            const double2 f = a.F[(size_t)l * a.n_x + x];
+            const double ml = a.m_t[l];
+            double2 ft = make_double2(f.x - ml * ap.x, f.y - ml * ap.y);
+            double2 kv = make_double2(0, 0);
+#pragma unroll
+            for (int d = 0; d < 5; ++d) {
+                const double bc = a.bsign * a.Bb[l * 5 + d];
+                const double mc = a.Mb[l * 5 + d];
+                // i * bc * P + mc * Q
+                kv.x += -bc * P[d].y + mc * Q[d].x;
+                kv.y += bc * P[d].x + mc * Q[d].y;
+            }
+            double2 r = make_double2(ft.x - kv.x, ft.y - kv.y);
+            if (a.R) a.R[(size_t)l * a.n_x + x] = r;
+            rr += r.x * r.x + r.y * r.y;
+            ff += ft.x * ft.x + ft.y * ft.y;
+        }
+    }
+    double s1 = block_sum(rr, red);
+    double s2 = block_sum(ff, red);
+    if (threadIdx.x == 0) {
+        const size_t bid = (size_t)blockIdx.y * gridDim.x + blockIdx.x;
+        a.partials[2 * bid] = s1;
+        a.partials[2 * bid + 1] = s2;
+    }
+}
+
+// scalars[0] = ||R||^2, [1] = ||F~||^2, [2] = scale = 2^e with 2^e * rms(R) in [1, 2), [3] = 1/scale
+__global__ void k_reduce_finalize(const double* partials, int nparts, double* scalars, double count) {
+    __shared__ double red[32];
+    double s1 = 0, s2 = 0;
+    for (int i = threadIdx.x; i < nparts; i += blockDim.x) {
+        s1 += partials[2 * i];
+        s2 += partials[2 * i + 1];
+    }
+    double t1 = block_sum(s1, red);
+    double t2 = block_sum(s2, red);
+    if (threadIdx.x == 0) {
+        scalars[0] = t1;
+        scalars[1] = t2;
+        double rms = sqrt(t1 / count);
+        double sc = 1.0;
+        if (rms > 0 && isfinite(rms)) {
+            int e;
+            frexp(rms, &e);          // rms = f 2^e, f in [0.5, 1)
+            sc = ldexp(1.0, 1 - e);  // sc * rms in [1, 2)
+        }
+        scalars[2] = sc;
+        scalars[3] = 1.0 / sc;
+    }
+}
+
+// psi[l, x] += psi0[x]
+template <typename T>
+__global__ void k_add_row(int n_t, int n_x, C<T>* psi, const C<T>* psi0) {
+    size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    size_t total = (size_t)n_t * n_x;
+    for (; i < total; i += (size_t)gridDim.x * blockDim.x) {
+        int x = (int)(i % n_x);
+        C<T> v = psi[i], p = psi0[x];
+        psi[i] = mk<T>(v.x + p.x, v.y + p.y);
+    }
+}
+
+// F[l, x] = sum_k Mfull[l+1, k] (M_x f_k)[x] over full time indices k (t_0 included)
+__global__ void k_load_nodal(int n_t, int n_x, Stencil s, const double* Mb, const double* Mfull0,
+                             const double2* f, double2* F) {
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    const int l = blockIdx.y;
+    if (x >= n_x || l >= n_t) return;
+    double2 acc = make_double2(0, 0);
+    // column t_0
+    {
+        double2 P, Q;
+        stencil_MA<double>(s, f, x, P, Q);
+        double c = Mfull0[l];
+        acc.x += c * P.x;
+        acc.y += c * P.y;
+    }
+    for (int d = -2; d <= 2; ++d) {
+        int k = l + d;  // reduced column index -> full row k + 1 of f
+        if (k < 0 || k >= n_t) continue;
+        double c = Mb[l * 5 + d + 2];
+        if (c == 0.0) continue;
+        double2 P, Q;
+        stencil_MA<double>(s, f + (size_t)(k + 1) * n_x, x, P, Q);
+        acc.x += c * P.x;
+        acc.y += c * P.y;
+    }
+    F[(size_t)l * n_x + x] = acc;
+}
+
+// out1[x] = sum_l U1[l, x];  out2[x] = sum_l w[l] U2[l, x]
+__global__ void k_colsums(int n_t, int n_x, const double2* U1, const double2* U2, const double* w, double2* out1,
+                          double2* out2) {
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    if (x >= n_x) return;
+    double2 a = make_double2(0, 0), b = make_double2(0, 0);
+    for (int l = 0; l < n_t; ++l) {
+        double2 u = U1[(size_t)l * n_x + x], v = U2[(size_t)l * n_x + x];
+        a.x += u.x;
+        a.y += u.y;
+        b.x += w[l] * v.x;
+        b.y += w[l] * v.y;
+    }
+    out1[x] = a;
+    out2[x] = b;
+}
+
+// ------------------------------------------------------------------ launchers
+static Stencil make_stencil(const SpaceMats& sm) {
+    return Stencil{sm.m, sm.Mc, sm.Mw, sm.Ms, sm.Md, sm.Ac, sm.Aw, sm.As, sm.Ad};
+}
+
+cudaError_t launch_stencil_A(const SpaceMats& sm, const void* in, bool in_c64, const double2* add, double sign,
+                             double2* out, cudaStream_t st) {
+    Stencil s = make_stencil(sm);
+    int grid = (sm.n_x + 255) / 256;
+    if (in_c64) k_stencil_A<float><<<grid, 256, 0, st>>>(s, sm.n_x, (const float2*)in, add, sign, out);
+    else k_stencil_A<double><<<grid, 256, 0, st>>>(s, sm.n_x, (const double2*)in, add, sign, out);
+    return cudaGetLastError();
+}
+
+int residual_num_partials(int n_t, int n_x) {
+    return ((n_x + 255) / 256) * ((n_t + RES_LT - 1) / RES_LT);
+}
+
+cudaError_t launch_residual(const SpaceMats& sm, int n_t, const double* Mb, const double* Bb, double bsign,
+                            const double2* F, const double2* apsi0, const double* m_t, const double2* U,
+                            const double2* psi0, double2* R, double* partials, double* scalars, cudaStream_t st) {
+    ResArgs a;
+    a.n_t = n_t;
+    a.n_x = sm.n_x;
+    a.s = make_stencil(sm);
+    a.Mb = Mb;
+    a.Bb = Bb;
+    a.bsign = bsign;
+    a.F = F;
+    a.apsi0 = apsi0;
+    a.m_t = m_t;
+    a.U = U;
+    a.psi0 = psi0;
+    a.R = R;
+    a.partials = partials;
+    dim3 grid((sm.n_x + 255) / 256, (n_t + RES_LT - 1) / RES_LT);
+    k_residual<<<grid, 256, 0, st>>>(a);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    k_reduce_finalize<<<1, 256, 0, st>>>(partials, (int)(grid.x * grid.y), scalars, (double)n_t * sm.n_x);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_add_row(int n_t, int n_x, void* psi, const void* psi0, bool c64, cudaStream_t st) {
+    size_t total = (size_t)n_t * n_x;
+    int grid = (int)std::min<size_t>((total + 255) / 256, 152 * 32);
+    if (c64) k_add_row<float><<<grid, 256, 0, st>>>(n_t, n_x, (float2*)psi, (const float2*)psi0);
+    else k_add_row<double><<<grid, 256, 0, st>>>(n_t, n_x, (double2*)psi, (const double2*)psi0);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_load_nodal(const SpaceMats& sm, int n_t, const double* Mb, const double* Mfull0,
+                              const double2* f, double2* F, cudaStream_t st) {
+    dim3 grid((sm.n_x + 255) / 256, n_t);
+    k_load_nodal<<<grid, 256, 0, st>>>(n_t, sm.n_x, make_stencil(sm), Mb, Mfull0, f, F);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_colsums(int n_t, int n_x, const double2* U1, const double2* U2, const double* w, double2* out1,
+                           double2* out2, cudaStream_t st) {
+    k_colsums<<<(n_x + 255) / 256, 256, 0, st>>>(n_t, n_x, U1, U2, w, out1, out2);
+    return cudaGetLastError();
+}
+
+}  // namespace stfdm

@@ -1,0 +1,268 @@
+"""Thin Python binding of the stfdm C ABI (include/stfdm.h), same entry-point names.
+
+Argument marshalling only: torch tensors provide device memory and the current
+CUDA stream; every step of the solver runs in the library's CUDA kernels.
+Space-time arrays are (n_t, n_x) contiguous complex tensors on the handle's
+device (complex128 for "fp64"/"mixed", complex64 for "fp32").
+"""
+from __future__ import annotations
+
+import ctypes
+
+import numpy as np
+import torch
+
+from . import _lib
+from ._lib import check, lib
+
+PREC = {"fp64": _lib.ST_FP64, "fp32": _lib.ST_FP32, "mixed": _lib.ST_MIXED}
+XFORM = {"Y": _lib.ST_XFORM_Y, "X": _lib.ST_XFORM_X, "XT": _lib.ST_XFORM_XT, "YT": _lib.ST_XFORM_YT}
+
+
+class _Handle:
+    _destroy = None
+
+    def __init__(self, ptr):
+        self.ptr = ptr
+
+    def __del__(self):
+        if self.ptr and self._destroy:
+            try:
+                getattr(lib(), self._destroy)(self.ptr)
+            except Exception:
+                pass
+            self.ptr = None
+
+
+class TimeHandle(_Handle):
+    _destroy = "st_destroy_time"
+
+
+class SpaceHandle(_Handle):
+    _destroy = "st_destroy_space"
+
+
+class FdmHandle(_Handle):
+    _destroy = "st_destroy_fdm"
+
+    def __init__(self, ptr, time, space):
+        super().__init__(ptr)
+        self.time = time
+        self.space = space
+        n_t, n_x, m = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+        kap, mni = ctypes.c_double(), ctypes.c_double()
+        check(lib().st_fdm_get(ptr, ctypes.byref(n_t), ctypes.byref(n_x), ctypes.byref(m), ctypes.byref(kap),
+                               ctypes.byref(mni)), "st_fdm_get")
+        self.n_t, self.n_x, self.m = n_t.value, n_x.value, m.value
+        self.kappa = kap.value
+        self.min_neg_im_shift = mni.value
+
+
+def _stream(stream):
+    if stream is None:
+        return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    if isinstance(stream, torch.cuda.Stream):
+        return ctypes.c_void_p(stream.cuda_stream)
+    return ctypes.c_void_p(int(stream))
+
+
+def _ptr(t):
+    return ctypes.c_void_p(t.data_ptr()) if t is not None else None
+
+
+def _check_st(h: FdmHandle, t, dtype, name):
+    if t is None:
+        return
+    if not t.is_cuda or t.dtype != dtype or not t.is_contiguous() or tuple(t.shape) != (h.n_t, h.n_x):
+        raise ValueError(f"{name}: expected a contiguous CUDA {dtype} tensor of shape {(h.n_t, h.n_x)}, "
+                         f"got {t.dtype} {tuple(t.shape)} on {t.device}")
+
+
+def _check_vec(h: FdmHandle, t, dtype, name):
+    if t is None:
+        return
+    if not t.is_cuda or t.dtype != dtype or not t.is_contiguous() or tuple(t.shape) != (h.n_x,):
+        raise ValueError(f"{name}: expected a contiguous CUDA {dtype} tensor of shape {(h.n_x,)}")
+
+
+def _dtype(precision):
+    return torch.complex64 if precision == "fp32" else torch.complex128
+
+
+def _opts(precision="fp64", tol=0.0, max_sweeps=0, keep_factors=-1, fixed_sweeps=0):
+    if precision not in PREC:
+        raise ValueError(f"unknown precision {precision!r}")
+    return _lib.st_solve_opts(PREC[precision], float(tol), int(max_sweeps), int(keep_factors), int(fixed_sweeps))
+
+
+def _info_dict(info: _lib.st_solve_info):
+    return dict(sweeps=info.sweeps, factors_kept=info.factors_kept, rel_residual=info.rel_residual,
+                residual_history=[v for v in info.residual_history if v >= 0], kappa_x=info.kappa_x,
+                min_neg_im_shift=info.min_neg_im_shift, setup_seconds=info.setup_seconds)
+
+
+# ------------------------------------------------------------------ assembly / setup
+def st_assemble_time(p_t: int, t_nodes) -> TimeHandle:
+    t = np.ascontiguousarray(np.asarray(t_nodes, dtype=np.float64))
+    out = ctypes.c_void_p()
+    check(lib().st_assemble_time(int(p_t), len(t) - 1, t.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                                 ctypes.byref(out)), "st_assemble_time")
+    return TimeHandle(out)
+
+
+def st_time_get(t: TimeHandle):
+    n = ctypes.c_int()
+    check(lib().st_time_get(t.ptr, ctypes.byref(n), None, None, None, None), "st_time_get")
+    n = n.value
+    M = np.zeros((n, n))
+    B = np.zeros((n, n))
+    m = np.zeros(n)
+    tt = np.zeros(n)
+    check(lib().st_time_get(t.ptr, None, M.ctypes.data, B.ctypes.data, m.ctypes.data, tt.ctypes.data),
+          "st_time_get")
+    return dict(M_t=M, B_t=B, m_t=m, times=tt)
+
+
+def st_assemble_space(n_squares: int, Lx: float = 1.0, Ly: float = 1.0) -> SpaceHandle:
+    out = ctypes.c_void_p()
+    check(lib().st_assemble_space(int(n_squares), float(Lx), float(Ly), ctypes.byref(out)), "st_assemble_space")
+    return SpaceHandle(out)
+
+
+def st_space_get(s: SpaceHandle):
+    m, n_x = ctypes.c_int(), ctypes.c_int()
+    coeffs = np.zeros(8)
+    check(lib().st_space_get(s.ptr, ctypes.byref(m), ctypes.byref(n_x), coeffs.ctypes.data), "st_space_get")
+    return m.value, n_x.value, coeffs
+
+
+def st_time_decompose(t: TimeHandle, host_threads: int = 0):
+    n = st_time_get(t)["M_t"].shape[0]
+    X = np.zeros((n, n), dtype=np.complex128)
+    Y = np.zeros((n, n), dtype=np.complex128)
+    s = np.zeros(n, dtype=np.complex128)
+    k = ctypes.c_double()
+    check(lib().st_time_decompose(t.ptr, int(host_threads), X.ctypes.data, s.ctypes.data, Y.ctypes.data,
+                                  ctypes.byref(k)), "st_time_decompose")
+    return X, s, Y, k.value
+
+
+def st_fdm_setup(t: TimeHandle, s: SpaceHandle, kappa_max: float = 0.0, device: int = -1,
+                 host_threads: int = 0) -> FdmHandle:
+    opts = _lib.st_setup_opts(float(kappa_max), int(device), int(host_threads))
+    out = ctypes.c_void_p()
+    check(lib().st_fdm_setup(t.ptr, s.ptr, ctypes.byref(opts), ctypes.byref(out)), "st_fdm_setup")
+    return FdmHandle(out, t, s)
+
+
+# ------------------------------------------------------------------ solves
+def st_fdm_solve(h: FdmHandle, F, psi0=None, psi=None, precision="fp64", tol=0.0, max_sweeps=0,
+                 keep_factors=-1, fixed_sweeps=0, stream=None, want_info=True):
+    dt = _dtype(precision)
+    _check_st(h, F, dt, "F")
+    _check_vec(h, psi0, dt, "psi0")
+    if psi is None:
+        psi = torch.empty_like(F)
+    _check_st(h, psi, dt, "psi")
+    opts = _opts(precision, tol, max_sweeps, keep_factors, fixed_sweeps)
+    info = _lib.st_solve_info()
+    check(lib().st_fdm_solve(h.ptr, _ptr(F), _ptr(psi0), _ptr(psi), ctypes.byref(opts),
+                             ctypes.byref(info) if want_info else None, _stream(stream)), "st_fdm_solve")
+    return psi, (_info_dict(info) if want_info else None)
+
+
+def st_residual(h: FdmHandle, F, psi0, psi, R=None, want_norm=True, stream=None):
+    _check_st(h, F, torch.complex128, "F")
+    _check_st(h, psi, torch.complex128, "psi")
+    _check_vec(h, psi0, torch.complex128, "psi0")
+    _check_st(h, R, torch.complex128, "R")
+    rel = ctypes.c_double(-1.0)
+    check(lib().st_residual(h.ptr, _ptr(F), _ptr(psi0), _ptr(psi), _ptr(R), ctypes.byref(rel) if want_norm else None,
+                            _stream(stream)), "st_residual")
+    return rel.value, R
+
+
+def st_adjoint_solve(h: FdmHandle, G, lam=None, precision="fp64", tol=0.0, max_sweeps=0, keep_factors=-1,
+                     fixed_sweeps=0, stream=None, want_info=True):
+    dt = _dtype(precision)
+    _check_st(h, G, dt, "G")
+    if lam is None:
+        lam = torch.empty_like(G)
+    _check_st(h, lam, dt, "lambda")
+    opts = _opts(precision, tol, max_sweeps, keep_factors, fixed_sweeps)
+    info = _lib.st_solve_info()
+    check(lib().st_adjoint_solve(h.ptr, _ptr(G), _ptr(lam), ctypes.byref(opts),
+                                 ctypes.byref(info) if want_info else None, _stream(stream)), "st_adjoint_solve")
+    return lam, (_info_dict(info) if want_info else None)
+
+
+def st_adjoint_lift(h: FdmHandle, grad_psi, grad_F, grad_psi0=None, stream=None):
+    _check_st(h, grad_psi, torch.complex128, "grad_psi")
+    _check_st(h, grad_F, torch.complex128, "grad_F")
+    if grad_psi0 is None:
+        grad_psi0 = torch.empty(h.n_x, dtype=torch.complex128, device=grad_psi.device)
+    _check_vec(h, grad_psi0, torch.complex128, "grad_psi0")
+    check(lib().st_adjoint_lift(h.ptr, _ptr(grad_psi), _ptr(grad_F), _ptr(grad_psi0), _stream(stream)),
+          "st_adjoint_lift")
+    return grad_psi0
+
+
+def st_fdm_solve_batched(hs, Fs, psi0s=None, psis=None, precision="fp64", tol=0.0, max_sweeps=0,
+                         keep_factors=-1, fixed_sweeps=0, stream=None, want_info=True):
+    n = len(hs)
+    dt = _dtype(precision)
+    if psis is None:
+        psis = [torch.empty_like(F) for F in Fs]
+    for h, F, p in zip(hs, Fs, psis):
+        _check_st(h, F, dt, "F")
+        _check_st(h, p, dt, "psi")
+    if psi0s is not None:
+        for h, p0 in zip(hs, psi0s):
+            _check_vec(h, p0, dt, "psi0")
+    H = (ctypes.c_void_p * n)(*[h.ptr for h in hs])
+    Fp = (ctypes.c_void_p * n)(*[F.data_ptr() for F in Fs])
+    Pp = (ctypes.c_void_p * n)(*[p.data_ptr() for p in psis])
+    P0 = (ctypes.c_void_p * n)(*[(p.data_ptr() if p is not None else None) for p in psi0s]) if psi0s else None
+    opts = _opts(precision, tol, max_sweeps, keep_factors, fixed_sweeps)
+    infos = (_lib.st_solve_info * n)()
+    check(lib().st_fdm_solve_batched(H, n, Fp, P0, Pp, ctypes.byref(opts), infos if want_info else None,
+                                     _stream(stream)), "st_fdm_solve_batched")
+    return psis, ([_info_dict(i) for i in infos] if want_info else None)
+
+
+def st_time_transform(h: FdmHandle, which: str, precision: str, inp, out=None, stream=None):
+    dt = _dtype(precision)
+    _check_st(h, inp, dt, "in")
+    if out is None:
+        out = torch.empty_like(inp)
+    _check_st(h, out, dt, "out")
+    check(lib().st_time_transform(h.ptr, XFORM[which], PREC[precision], _ptr(inp), _ptr(out), _stream(stream)),
+          "st_time_transform")
+    return out
+
+
+def st_spatial_solve(h: FdmHandle, precision: str, G, W=None, stream=None):
+    dt = _dtype(precision)
+    _check_st(h, G, dt, "G")
+    if W is None:
+        W = torch.empty_like(G)
+    _check_st(h, W, dt, "W")
+    check(lib().st_spatial_solve(h.ptr, PREC[precision], _ptr(G), _ptr(W), _stream(stream)), "st_spatial_solve")
+    return W
+
+
+def st_load_nodal(h: FdmHandle, f_nodal, F=None, stream=None):
+    if not f_nodal.is_cuda or f_nodal.dtype != torch.complex128 or tuple(f_nodal.shape) != (h.n_t + 1, h.n_x):
+        raise ValueError("f_nodal: expected a CUDA complex128 tensor of shape (n_t + 1, n_x)")
+    f_nodal = f_nodal.contiguous()
+    if F is None:
+        F = torch.empty((h.n_t, h.n_x), dtype=torch.complex128, device=f_nodal.device)
+    check(lib().st_load_nodal(h.ptr, _ptr(f_nodal), _ptr(F), _stream(stream)), "st_load_nodal")
+    return F
+
+
+def setup_problem(n_squares: int, p_t: int, t_nodes, Lx: float = 1.0, Ly: float = 1.0, **kw) -> FdmHandle:
+    """assemble_time + assemble_space + fdm_setup in one call."""
+    t = st_assemble_time(p_t, t_nodes)
+    s = st_assemble_space(n_squares, Lx, Ly)
+    return st_fdm_setup(t, s, **kw)

@@ -1,0 +1,83 @@
+"""Full-size checks at the benchmark workload (256x256 squares, P1 time on 512 uniform
+elements, T = 1: 33,292,800 unknowns) in the launch configuration the benchmark times.
+
+The oracle cannot solve this size directly, so it checks what holds at any size:
+  * the oracle builds the inputs (interpolated load of the manufactured problem);
+  * the oracle's FP64 Kronecker residual of the GPU's mixed-precision solution;
+  * sampled spatial solves (three eigen-indices) against SuperLU, FP32 and FP64;
+  * mixed precision against the GPU FP64 FDM on the same inputs (<= 1e-9, the metric's bar).
+"""
+import numpy as np
+import pytest
+import scipy.sparse as sp
+import scipy.sparse.linalg as spla
+
+import synth
+from oracle import fe_space, fe_time, solve
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def c2():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2504_07269_gb300 import build, stfdm
+
+    build.build()
+    pr = synth.config_problem("c2")
+    h = stfdm.setup_problem(pr.n, pr.p_t, pr.t_nodes, device=0)
+    M_t, B_t, m_t, times = fe_time.assemble_time(pr.p_t, pr.t_nodes)
+    Mf, _, tfull = fe_time.assemble_time_full(pr.p_t, pr.t_nodes)
+    M_x, A_x = fe_space.assemble_space(pr.n)
+    x1, x2 = synth.interior_coords(pr.n)
+    f = synth.f_c1(x1[None, :], x2[None, :], tfull[:, None])
+    F = Mf[1:] @ (M_x @ f.T).T                   # oracle: interpolated load (M_t,full (x) M_x) f
+    psi0 = synth.psi0_c1(x1, x2)
+    return dict(pr=pr, h=h, M_t=M_t, B_t=B_t, m_t=m_t, M_x=M_x, A_x=A_x, F=F, psi0=psi0, times=times)
+
+
+def test_fullsize_mixed_residual_and_vs_fp64(c2):
+    from paper_2504_07269_gb300 import stfdm
+
+    dev = torch.device("cuda:0")
+    h = c2["h"]
+    Fd = torch.from_numpy(c2["F"]).to(dev)
+    p0 = torch.from_numpy(c2["psi0"]).to(dev)
+    psi, info = stfdm.st_fdm_solve(h, Fd, p0, precision="mixed")
+    U = psi.cpu().numpy()
+    Ft = c2["F"] - np.outer(c2["m_t"], c2["A_x"] @ c2["psi0"])
+    _, r = solve.residual(c2["M_t"], c2["B_t"], c2["M_x"], c2["A_x"], U - c2["psi0"][None, :], Ft)
+    print(f"c2 mixed: sweeps {info['sweeps']}, library residual {info['rel_residual']:.2e}, oracle residual {r:.2e}")
+    assert r <= 1e-11
+    psi64, _ = stfdm.st_fdm_solve(h, Fd, p0, precision="fp64")
+    U64 = psi64.cpu().numpy()
+    err = np.linalg.norm(U - U64) / np.linalg.norm(U64)
+    print(f"c2 mixed vs fp64: {err:.2e}")
+    assert err <= 1e-9
+    _, r64 = solve.residual(c2["M_t"], c2["B_t"], c2["M_x"], c2["A_x"], U64 - c2["psi0"][None, :], Ft)
+    assert r64 <= 1e-10
+    # discretisation check: the solution is close to the manufactured psi
+    x1, x2 = synth.interior_coords(c2["pr"].n)
+    ex = synth.psi_c1(x1[None, :], x2[None, :], c2["times"][:, None])
+    assert np.abs(U - ex).max() < 1e-3
+
+
+def test_fullsize_sampled_spatial_solves(c2):
+    from paper_2504_07269_gb300 import stfdm
+
+    dev = torch.device("cuda:0")
+    h = c2["h"]
+    _, s, _, _ = stfdm.st_time_decompose(h.time)
+    G = synth.cn01((h.n_t, h.n_x), seed=77)
+    ks = [0, h.n_t // 2, h.n_t - 1]
+    refs = {k: spla.splu(sp.csc_matrix(c2["M_x"] + s[k] * c2["A_x"], dtype=np.complex128)).solve(G[k]) for k in ks}
+    W32 = stfdm.st_spatial_solve(h, "fp32", torch.from_numpy(G).to(dev).to(torch.complex64)).cpu().numpy()
+    W64 = stfdm.st_spatial_solve(h, "fp64", torch.from_numpy(G).to(dev)).cpu().numpy()
+    for k in ks:
+        e64 = np.linalg.norm(W64[k] - refs[k]) / np.linalg.norm(refs[k])
+        e32 = np.linalg.norm(W32[k] - refs[k]) / np.linalg.norm(refs[k])
+        print(f"k={k} s={s[k]:.3e}: fp64 {e64:.2e} fp32 {e32:.2e}")
+        assert e64 <= 1e-11
+        assert e32 <= 1e-2
