@@ -51,6 +51,8 @@ def parse_args(argv=None):
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64", "fp32"])
     ap.add_argument("--no-fp64-check", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--profile-step", action="store_true",
+                    help="set up, then run exactly one solve and exit (for ncu launch lists)")
     return ap.parse_args(argv)
 
 
@@ -261,6 +263,12 @@ def run_ours(args):
     p0 = p0.to(dt)
     psi = torch.empty_like(F)
     info = {}
+    if args.profile_step:
+        _, info = stfdm.st_fdm_solve(h, F, p0, psi=psi, precision=args.precision)
+        torch.cuda.synchronize()
+        if rank == 0:
+            print(json.dumps({"profile_step": args.config, "precision": args.precision, "info": info}))
+        return 0
 
     def step():
         nonlocal info

@@ -89,12 +89,22 @@ typedef struct {
 typedef struct {
     int precision;      /* ST_FP64, ST_FP32 or ST_MIXED */
     double tol;         /* ST_MIXED: stop when ||F~ - K psi_hat||_2 / ||F~||_2 <= tol; <= 0 selects 1e-12 */
-    int max_sweeps;     /* ST_MIXED: at most this many FDM sweeps; <= 0 selects 12 */
+    int max_sweeps;     /* ST_MIXED: at most this many FDM32 applications; <= 0 selects 40 */
     int keep_factors;   /* ST_MIXED: 1 = store all n_t LDL^T factors and reuse them in later sweeps
                            when they fit the memory budget, 0 = refactor every sweep, -1 = automatic */
-    int fixed_sweeps;   /* ST_MIXED: > 0 runs exactly this many sweeps with no host synchronisation
-                           (no convergence test; the final residual is still reported) */
+    int fixed_sweeps;   /* ST_MIXED: > 0 runs exactly this many classical refinement sweeps with no
+                           host synchronisation (no convergence test; the final residual is reported
+                           when info is non-NULL) */
+    int method;         /* ST_MIXED: ST_REFINE_GMRES (default) or ST_REFINE_CLASSIC */
 } st_solve_opts;
+
+/* refinement methods of ST_MIXED.  Both compute the residual in FP64 and correct with the
+ * complex-FP32 FDM.  CLASSIC: psi += FDM32(R) each sweep.  GMRES: flexible GMRES in FP64,
+ * right-preconditioned by FDM32 (restarted); a few eigen-indices whose shifted spatial matrix
+ * is nearly singular in FP32 slow the classical sweeps down, GMRES removes them in a few
+ * extra iterations.  max_sweeps counts FDM32 applications in both. */
+#define ST_REFINE_GMRES   0
+#define ST_REFINE_CLASSIC 1
 
 typedef struct {
     int sweeps;                  /* FDM sweeps run (1 for ST_FP64 / ST_FP32) */

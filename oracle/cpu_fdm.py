@@ -42,8 +42,19 @@ def spatial_solves(n, s, G, Lx=1.0, Ly=1.0, workers=None):
     """w_k = (M_x + s_k A_x)^{-1} g_k for all k, over a 'spawn' process pool."""
     workers = workers or os.cpu_count()
     ctx = mp.get_context("spawn")
-    with ctx.Pool(workers, initializer=_init, initargs=(n, Lx, Ly)) as pool:
-        out = pool.map(_solve_one, [(s[k], G[k]) for k in range(len(s))], chunksize=1)
+    # one BLAS thread per worker: the children read these when they import numpy/scipy
+    saved = {k: os.environ.get(k) for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS")}
+    for k in saved:
+        os.environ[k] = "1"
+    try:
+        with ctx.Pool(workers, initializer=_init, initargs=(n, Lx, Ly)) as pool:
+            out = pool.map(_solve_one, [(s[k], G[k]) for k in range(len(s))], chunksize=1)
+    finally:
+        for k, v in saved.items():
+            if v is None:
+                os.environ.pop(k, None)
+            else:
+                os.environ[k] = v
     return np.stack(out)
 
 

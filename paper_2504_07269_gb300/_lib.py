@@ -28,6 +28,9 @@ ST_FP64 = 0
 ST_FP32 = 1
 ST_MIXED = 2
 
+ST_REFINE_GMRES = 0
+ST_REFINE_CLASSIC = 1
+
 ST_XFORM_Y = 0
 ST_XFORM_X = 1
 ST_XFORM_XT = 2
@@ -40,7 +43,7 @@ class st_setup_opts(ctypes.Structure):
 
 class st_solve_opts(ctypes.Structure):
     _fields_ = [("precision", c_int), ("tol", c_double), ("max_sweeps", c_int), ("keep_factors", c_int),
-                ("fixed_sweeps", c_int)]
+                ("fixed_sweeps", c_int), ("method", c_int)]
 
 
 class st_solve_info(ctypes.Structure):
@@ -101,6 +104,8 @@ def lib():
 
 
 class StfdmError(RuntimeError):
+    info = None
+
     def __init__(self, status: int, where: str):
         L = lib()
         msg = L.st_last_error_message()

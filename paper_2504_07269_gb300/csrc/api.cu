@@ -27,6 +27,14 @@ cudaError_t launch_load_nodal(const SpaceMats& sm, int n_t, const double* Mb, co
                               const double2* f, double2* F, cudaStream_t st);
 cudaError_t launch_colsums(int n_t, int n_x, const double2* U1, const double2* U2, const double* w, double2* out1,
                            double2* out2, cudaStream_t st);
+cudaError_t launch_multidot(const double2* const* Vdev, int nv, const double2* w, size_t n, double2* partial,
+                            double2* out, cudaStream_t st);
+cudaError_t launch_multiaxpy(const double2* const* Vdev, int nv, const double2* c, double sign, double2* y, size_t n,
+                             cudaStream_t st);
+cudaError_t launch_scale(const double2* x, double alpha, double2* y, size_t n, cudaStream_t st);
+cudaError_t launch_set_scalars(double* dst, double a, double b, cudaStream_t st);
+int krylov_partial_count();
+int krylov_max_vectors();
 
 }  // namespace stfdm
 
@@ -111,6 +119,9 @@ void free_handle(st_fdm* h) {
     cudaFree(h->ws_vec);
     cudaFree(h->ws_red);
     cudaFree(h->ws_status);
+    cudaFree(h->ws_kry);
+    cudaFree(h->kry_ptrs);
+    cudaFree(h->kry_small);
     delete h;
 }
 
@@ -149,8 +160,16 @@ const double2* shifts_of<double>(const st_fdm* h) { return h->s64; }
 template <>
 const float2* shifts_of<float>(const st_fdm* h) { return h->s32; }
 
-// mode: 0 = factor and solve (transient factors), 1 = factor, keep all factors, and solve,
-//       2 = solve with kept factors
+bool factors_fit(st_fdm* h, size_t elem) {
+    size_t freeb = 0, total = 0;
+    if (cudaMemGetInfo(&freeb, &total) != cudaSuccess) return false;
+    const size_t need = (size_t)h->tm.n_t * h->sm.n_x * (size_t)(h->sm.m + 1 + 1) * elem;
+    size_t have = h->ws_L_bytes + h->ws_D_bytes;
+    return need <= (size_t)(0.85 * (double)(freeb + have));
+}
+
+// mode: 0 = factor and solve (factors transient, in chunks of systems), 1 = factor, keep all
+//       factors, and solve, 2 = forward + backward substitution with the kept factors
 template <typename T>
 st_status band_run(st_fdm* h, C<T>* G, int mode, cudaStream_t st) {
     const SpaceMats& sm = h->sm;
@@ -165,6 +184,7 @@ st_status band_run(st_fdm* h, C<T>* G, int mode, cudaStream_t st) {
     a.m = sm.m;
     a.b = b;
     a.n_sys = n_t;
+    a.k0 = 0;
     a.Mc = (T)sm.Mc; a.Mw = (T)sm.Mw; a.Ms = (T)sm.Ms; a.Md = (T)sm.Md;
     a.Ac = (T)sm.Ac; a.Aw = (T)sm.Aw; a.As = (T)sm.As; a.Ad = (T)sm.Ad;
     a.shifts = shifts_of<T>(h);
@@ -178,22 +198,31 @@ st_status band_run(st_fdm* h, C<T>* G, int mode, cudaStream_t st) {
         a.L = reinterpret_cast<C<T>*>(h->ws_L);
         a.D = reinterpret_cast<C<T>*>(h->ws_D);
         a.keep = 1;
-        CUDA_TRY(band_solve_launch<T>(a, nb, grid, st));
+        CUDA_TRY(subst_launch<T>(a, 0, n_t, true, st));
+        CUDA_TRY(subst_launch<T>(a, 0, n_t, false, st));
         return ST_OK;
     }
     st_status s = grow(h->ws_win, h->ws_win_bytes, (size_t)grid * WR * (b + 1) * sizeof(C<T>), "band windows");
     if (s != ST_OK) return s;
-    const size_t slots = (mode == 1) ? (size_t)n_t : (size_t)grid;
-    s = grow(h->ws_L, h->ws_L_bytes, slots * n * b * sizeof(C<T>), "band factors");
+    // transient factors: all systems in one launch when their factors fit, else chunks of `grid`
+    int chunk = (mode == 1) ? n_t : grid;
+    if (mode == 0 && chunk < n_t && factors_fit(h, sizeof(C<T>))) chunk = n_t;
+    s = grow(h->ws_L, h->ws_L_bytes, (size_t)chunk * n * b * sizeof(C<T>), "band factors");
     if (s != ST_OK) return s;
-    s = grow(h->ws_D, h->ws_D_bytes, slots * n * sizeof(C<T>), "band pivots");
+    s = grow(h->ws_D, h->ws_D_bytes, (size_t)chunk * n * sizeof(C<T>), "band pivots");
     if (s != ST_OK) return s;
     h->factors_valid = 0;
     a.win = reinterpret_cast<C<T>*>(h->ws_win);
     a.L = reinterpret_cast<C<T>*>(h->ws_L);
     a.D = reinterpret_cast<C<T>*>(h->ws_D);
     a.keep = (mode == 1) ? 1 : 0;
-    CUDA_TRY(band_factor_solve_launch<T>(a, nb, grid, st));
+    for (int k0 = 0; k0 < n_t; k0 += chunk) {
+        const int cnt = std::min(chunk, n_t - k0);
+        a.k0 = k0;
+        a.n_sys = cnt;
+        CUDA_TRY(band_factor_solve_launch<T>(a, nb, std::min(grid, cnt), st));
+        CUDA_TRY(subst_launch<T>(a, k0, cnt, false, st));
+    }
     if (mode == 1) {
         h->factors_valid = 1;
         h->factors_prec = (int)sizeof(T);
@@ -261,13 +290,6 @@ st_status solve_fp32(st_fdm* h, const void* F, const void* psi0, void* psi, cuda
                                              nullptr, nullptr, psi0, nullptr, nullptr, st);
 }
 
-bool factors_fit(st_fdm* h, size_t elem) {
-    size_t freeb = 0, total = 0;
-    if (cudaMemGetInfo(&freeb, &total) != cudaSuccess) return false;
-    const size_t need = (size_t)h->tm.n_t * h->sm.n_x * (size_t)(h->sm.m + 1 + 1) * elem;
-    size_t have = h->ws_L_bytes + h->ws_D_bytes;
-    return need <= (size_t)(0.85 * (double)(freeb + have));
-}
 
 // Mixed precision: complex-FP32 FDM sweeps on the FP64 residual (forward: K, adjoint: K^H).
 st_status solve_mixed(st_fdm* h, bool adjoint, const void* F, const void* psi0, void* psi, const st_solve_opts& o,
@@ -367,6 +389,218 @@ st_status solve_mixed(st_fdm* h, bool adjoint, const void* F, const void* psi0, 
     return ST_OK;
 }
 
+
+// ------------------------------------------------------------------ GMRES-based refinement
+// FP64 flexible GMRES(m) for K x = F~ (or K^H x = G), right-preconditioned by the complex-FP32
+// FDM: z = FDM32(v).  The Arnoldi basis V, the directions Z, the operator apply and the
+// orthogonalisation (classical Gram-Schmidt, done twice) are FP64 on the device; the small
+// Hessenberg least-squares problem (Givens rotations) is solved on the host.
+st_status precond32(st_fdm* h, bool adjoint, const double2* v, double2* z, bool& keep, bool& first,
+                    const double* scal, cudaStream_t st) {
+    const int n_t = h->tm.n_t, n_x = h->sm.n_x;
+    float2* G = reinterpret_cast<float2*>(h->ws_g32);
+    st_status s;
+    if (!adjoint)
+        s = xform<float, double, float, float>(reinterpret_cast<float*>(h->xf32[XF_Y]), n_t, n_x, v, G, 0, 0, 0,
+                                               scal, nullptr, nullptr, nullptr, nullptr, st);
+    else
+        s = xform<float, double, float, float>(reinterpret_cast<float*>(h->xf32[XF_XT]), n_t, n_x, v, G, 1, 0, 0,
+                                               scal, nullptr, nullptr, nullptr, nullptr, st);
+    if (s != ST_OK) return s;
+    int mode = keep ? (first ? 1 : 2) : 0;
+    s = band_run<float>(h, G, mode, st);
+    if (s == ST_ERR_OOM && mode == 1) {
+        s = band_run<float>(h, G, 0, st);
+        keep = false;
+    }
+    if (s != ST_OK) return s;
+    first = false;
+    if (!adjoint)
+        return xform<float, float, double, float>(reinterpret_cast<float*>(h->xf32[XF_X]), n_t, n_x, G, z, 0, 0, 0,
+                                                  nullptr, scal + 1, nullptr, nullptr, nullptr, st);
+    return xform<float, float, double, float>(reinterpret_cast<float*>(h->xf32[XF_YT]), n_t, n_x, G, z, 0, 1, 0,
+                                              nullptr, scal + 1, nullptr, nullptr, nullptr, st);
+}
+
+st_status ensure_krylov(st_fdm* h, int m) {
+    const size_t N = (size_t)h->tm.n_t * h->sm.n_x;
+    const size_t need = (size_t)(2 * m + 1) * N * sizeof(double2);
+    st_status s = grow(h->ws_kry, h->ws_kry_bytes, need, "GMRES basis");
+    if (s != ST_OK) return s;
+    if (!h->kry_ptrs) {
+        s = dev_alloc(reinterpret_cast<void**>(&h->kry_ptrs), sizeof(double2*) * 2 * (krylov_max_vectors() + 1),
+                      "GMRES pointers");
+        if (s != ST_OK) return s;
+    }
+    s = grow(h->kry_small, h->kry_small_bytes, sizeof(double2) * (krylov_partial_count() + 4 * krylov_max_vectors()),
+             "GMRES scalars");
+    if (s != ST_OK) return s;
+    std::vector<double2*> ptrs(2 * m + 2);
+    double2* base = reinterpret_cast<double2*>(h->ws_kry);
+    for (int i = 0; i < 2 * m + 1; ++i) ptrs[i] = base + (size_t)i * N;
+    ptrs[2 * m + 1] = reinterpret_cast<double2*>(h->ws_big);  // w (shares the residual buffer)
+    CUDA_TRY(cudaMemcpy(h->kry_ptrs, ptrs.data(), sizeof(double2*) * ptrs.size(), cudaMemcpyHostToDevice));
+    h->kry_m = m;
+    return ST_OK;
+}
+
+st_status solve_mixed_gmres(st_fdm* h, bool adjoint, const void* F, const void* psi0, void* psi,
+                            const st_solve_opts& o, st_solve_info* info, cudaStream_t st) {
+    const int n_t = h->tm.n_t, n_x = h->sm.n_x;
+    const size_t N = (size_t)n_t * n_x;
+    st_status s = ensure_common(h);
+    if (s != ST_OK) return s;
+    s = grow(h->ws_big, h->ws_big_bytes, N * sizeof(double2), "R");
+    if (s != ST_OK) return s;
+    s = grow(h->ws_g32, h->ws_g32_bytes, N * sizeof(float2), "G32");
+    if (s != ST_OK) return s;
+    const double tol = o.tol > 0 ? o.tol : 1e-12;
+    const int maxit = o.max_sweeps > 0 ? o.max_sweeps : 40;
+    bool keep = false;
+    if (o.keep_factors == 1) keep = true;
+    else if (o.keep_factors == -1) keep = factors_fit(h, sizeof(float2));
+    // restart length: at most 20, and the basis within a quarter of the free memory
+    int m = std::min(20, krylov_max_vectors() - 1);
+    {
+        size_t freeb = 0, total = 0;
+        cudaMemGetInfo(&freeb, &total);
+        size_t avail = freeb + h->ws_kry_bytes;
+        if (keep) {
+            const size_t fac = (size_t)n_t * n_x * (size_t)(h->sm.m + 2) * sizeof(float2);
+            avail = avail > fac + h->ws_L_bytes ? avail - (fac > h->ws_L_bytes ? fac - h->ws_L_bytes : 0) : 0;
+        }
+        while (m > 2 && (size_t)(2 * m + 1) * N * sizeof(double2) > avail / 3) --m;
+    }
+    s = ensure_krylov(h, m);
+    if (s != ST_OK) return s;
+    double2* const* P = h->kry_ptrs;                 // device pointer array
+    double2* V0 = reinterpret_cast<double2*>(h->ws_kry);
+    auto Vp = [&](int i) { return V0 + (size_t)i * N; };
+    auto Zp = [&](int i) { return V0 + (size_t)(m + 1 + i) * N; };
+    double2* w = reinterpret_cast<double2*>(h->ws_big);
+    double2* partial = reinterpret_cast<double2*>(h->kry_small);
+    double2* hb = partial + krylov_partial_count();   // 4 coefficient buffers of KRY_MAXV
+    const int MV = krylov_max_vectors();
+    double* scal = h->ws_red;       // [0..3] residual scalars, [4..5] preconditioner scaling
+    double* parts = h->ws_red + 8;
+    double2* apsi0 = nullptr;
+    if (psi0 && !adjoint) {
+        apsi0 = vec_slot(h, 0);
+        CUDA_TRY(launch_stencil_A(h->sm, psi0, false, nullptr, 1.0, apsi0, st));
+    }
+    const double* Bband = adjoint ? h->dt.BTb : h->dt.Bb;
+    const double bsign = adjoint ? -1.0 : 1.0;
+    // unit-norm basis vectors have entries ~ N^{-1/2}: scale by a power of two near sqrt(N) for FP32
+    const double psc = std::ldexp(1.0, (int)std::lround(0.5 * std::log2((double)N)));
+    CUDA_TRY(launch_set_scalars(scal + 4, psc, 1.0 / psc, st));
+    CUDA_TRY(cudaMemsetAsync(psi, 0, N * sizeof(double2), st));
+    CUDA_TRY(cudaMemsetAsync(h->ws_status, 0, sizeof(int), st));
+    double2* x = reinterpret_cast<double2*>(psi);
+    double hist[16];
+    int nh = 0;
+    int its = 0;
+    double bnorm = -1, rel = -1;
+    bool converged = false, first = true, x_zero = true;
+    std::vector<cd> H((size_t)(m + 1) * m), g(m + 1), sn(m);
+    std::vector<double> cs(m);
+    std::vector<double2> hh(3 * MV);
+    while (true) {
+        CUDA_TRY(launch_residual(h->sm, n_t, h->dt.Mb, Bband, bsign, reinterpret_cast<const double2*>(F), apsi0,
+                                 h->dt.m, x_zero ? nullptr : x, nullptr, w, parts, scal, st));
+        double hs[2];
+        CUDA_TRY(cudaMemcpyAsync(hs, scal, 2 * sizeof(double), cudaMemcpyDeviceToHost, st));
+        CUDA_TRY(cudaStreamSynchronize(st));
+        const double beta = std::sqrt(hs[0]);
+        if (bnorm < 0) bnorm = std::sqrt(hs[1]);
+        rel = bnorm > 0 ? beta / bnorm : 0.0;
+        if (nh < 15) hist[nh++] = rel;
+        if (!std::isfinite(rel)) return fail(ST_ERR_NOT_CONVERGED, "refinement: non-finite residual");
+        if (rel <= tol || beta == 0.0) {
+            converged = true;
+            break;
+        }
+        if (its >= maxit) break;
+        CUDA_TRY(launch_scale(w, 1.0 / beta, Vp(0), N, st));
+        std::fill(g.begin(), g.end(), cd(0));
+        g[0] = beta;
+        int jdone = 0;
+        for (int j = 0; j < m; ++j) {
+            s = precond32(h, adjoint, Vp(j), Zp(j), keep, first, scal + 4, st);
+            if (s != ST_OK) return s;
+            ++its;
+            // w = K z_j (operator apply: no right-hand side)
+            CUDA_TRY(launch_residual(h->sm, n_t, h->dt.Mb, Bband, bsign, nullptr, nullptr, h->dt.m, Zp(j), nullptr,
+                                     w, parts, scal, st));
+            // two passes of classical Gram-Schmidt, then ||w||
+            CUDA_TRY(launch_multidot(P, j + 1, w, N, partial, hb, st));
+            CUDA_TRY(launch_multiaxpy(P, j + 1, hb, -1.0, w, N, st));
+            CUDA_TRY(launch_multidot(P, j + 1, w, N, partial, hb + MV, st));
+            CUDA_TRY(launch_multiaxpy(P, j + 1, hb + MV, -1.0, w, N, st));
+            CUDA_TRY(launch_multidot(P + 2 * m + 1, 1, w, N, partial, hb + 2 * MV, st));
+            CUDA_TRY(cudaMemcpyAsync(hh.data(), hb, 3 * MV * sizeof(double2), cudaMemcpyDeviceToHost, st));
+            CUDA_TRY(cudaStreamSynchronize(st));
+            const double hn = std::sqrt(std::max(0.0, hh[2 * MV].x));
+            for (int i = 0; i <= j; ++i)
+                H[(size_t)i * m + j] = cd(hh[i].x + hh[MV + i].x, hh[i].y + hh[MV + i].y);
+            H[(size_t)(j + 1) * m + j] = hn;
+            // previous rotations, then the new one (G = [[c, s], [-conj s, c]])
+            for (int i = 0; i < j; ++i) {
+                cd a = H[(size_t)i * m + j], b = H[(size_t)(i + 1) * m + j];
+                H[(size_t)i * m + j] = cs[i] * a + sn[i] * b;
+                H[(size_t)(i + 1) * m + j] = -std::conj(sn[i]) * a + cs[i] * b;
+            }
+            {
+                cd a = H[(size_t)j * m + j], b = H[(size_t)(j + 1) * m + j];
+                double aa = std::abs(a), ab = std::abs(b);
+                if (ab == 0.0) {
+                    cs[j] = 1.0;
+                    sn[j] = 0.0;
+                } else if (aa == 0.0) {
+                    cs[j] = 0.0;
+                    sn[j] = std::conj(b) / ab;
+                } else {
+                    double rho = std::hypot(aa, ab);
+                    cs[j] = aa / rho;
+                    sn[j] = (a / aa) * std::conj(b) / rho;
+                }
+                H[(size_t)j * m + j] = cs[j] * a + sn[j] * b;
+                H[(size_t)(j + 1) * m + j] = 0.0;
+                cd gj = g[j];
+                g[j] = cs[j] * gj;
+                g[j + 1] = -std::conj(sn[j]) * gj;
+            }
+            jdone = j + 1;
+            const double est = std::abs(g[j + 1]) / bnorm;
+            if (est <= 0.5 * tol || j == m - 1 || its >= maxit || hn <= 1e-300) break;
+            CUDA_TRY(launch_scale(w, 1.0 / hn, Vp(j + 1), N, st));
+        }
+        // y = R^{-1} g, x += Z y
+        std::vector<cd> y(jdone);
+        for (int i = jdone - 1; i >= 0; --i) {
+            cd acc = g[i];
+            for (int k = i + 1; k < jdone; ++k) acc -= H[(size_t)i * m + k] * y[k];
+            y[i] = acc / H[(size_t)i * m + i];
+        }
+        std::vector<double2> yd(jdone);
+        for (int i = 0; i < jdone; ++i) yd[i] = make_double2(y[i].real(), y[i].imag());
+        CUDA_TRY(cudaMemcpyAsync(hb + 3 * MV, yd.data(), jdone * sizeof(double2), cudaMemcpyHostToDevice, st));
+        CUDA_TRY(launch_multiaxpy(P + m + 1, jdone, hb + 3 * MV, 1.0, x, N, st));
+        CUDA_TRY(cudaStreamSynchronize(st));  // yd lives on the host stack
+        x_zero = false;
+    }
+    if (psi0 && !adjoint) CUDA_TRY(launch_add_row(n_t, n_x, psi, psi0, false, st));
+    if (info) {
+        info->sweeps = its;
+        info->factors_kept = keep ? 1 : 0;
+        info->rel_residual = rel;
+        for (int i = 0; i < 16; ++i) info->residual_history[i] = (i < nh) ? hist[i] : -1.0;
+    }
+    s = check_status_flag(h, st);
+    if (s != ST_OK) return s;
+    if (!converged) return fail(ST_ERR_NOT_CONVERGED, "refinement: tolerance not reached in max_sweeps");
+    return ST_OK;
+}
+
 st_status adjoint_direct(st_fdm* h, bool fp32, const void* G, void* lambda, cudaStream_t st) {
     const int n_t = h->tm.n_t, n_x = h->sm.n_x;
     st_status s;
@@ -402,6 +636,8 @@ st_status validate_opts(const st_solve_opts* o, st_solve_opts& out) {
     out = o ? *o : d;
     if (out.precision != ST_FP64 && out.precision != ST_FP32 && out.precision != ST_MIXED)
         return fail(ST_ERR_ARG, "solve: unknown precision");
+    if (out.method != ST_REFINE_GMRES && out.method != ST_REFINE_CLASSIC)
+        return fail(ST_ERR_ARG, "solve: unknown refinement method");
     return ST_OK;
 }
 
@@ -553,7 +789,10 @@ extern "C" st_status st_fdm_solve(st_fdm* h, const void* F, const void* psi0, vo
     DeviceGuard g(h->device);
     cudaStream_t st = S(stream);
     fill_info_common(h, info);
-    if (o.precision == ST_MIXED) return solve_mixed(h, false, F, psi0, psi, o, info, st);
+    if (o.precision == ST_MIXED) {
+        if (o.fixed_sweeps > 0 || o.method == ST_REFINE_CLASSIC) return solve_mixed(h, false, F, psi0, psi, o, info, st);
+        return solve_mixed_gmres(h, false, F, psi0, psi, o, info, st);
+    }
     CUDA_TRY(cudaMemsetAsync(h->ws_status, 0, sizeof(int), st));
     s = (o.precision == ST_FP64) ? solve_fp64(h, F, psi0, psi, st) : solve_fp32(h, F, psi0, psi, st);
     if (s != ST_OK) return s;
@@ -603,7 +842,10 @@ extern "C" st_status st_adjoint_solve(st_fdm* h, const void* G, void* lambda, co
     DeviceGuard g(h->device);
     cudaStream_t st = S(stream);
     fill_info_common(h, info);
-    if (o.precision == ST_MIXED) return solve_mixed(h, true, G, nullptr, lambda, o, info, st);
+    if (o.precision == ST_MIXED) {
+        if (o.fixed_sweeps > 0 || o.method == ST_REFINE_CLASSIC) return solve_mixed(h, true, G, nullptr, lambda, o, info, st);
+        return solve_mixed_gmres(h, true, G, nullptr, lambda, o, info, st);
+    }
     CUDA_TRY(cudaMemsetAsync(h->ws_status, 0, sizeof(int), st));
     s = adjoint_direct(h, o.precision == ST_FP32, G, lambda, st);
     if (s != ST_OK) return s;

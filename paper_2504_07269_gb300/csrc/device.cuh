@@ -82,21 +82,22 @@ struct BandArgs {
     int n;          // n_x
     int m;          // interior nodes per grid row
     int b;          // half bandwidth m + 1
-    int n_sys;      // number of systems (n_t)
+    int n_sys;      // number of systems in this launch
+    int k0;         // index of the first system
     T Mc, Mw, Ms, Md, Ac, Aw, As, Ad;   // stencil coefficients of M_x and A_x
     const C<T>* shifts;   // s_k
     C<T>* rhs;            // (n_sys, n): g_k in, w_k out
     C<T>* win;            // gridDim.x windows of (b + NB) x (b + 1)
     C<T>* L;              // factor columns: L[j*b + o - 1] = L(j + o, j), o = 1..b
     C<T>* D;              // pivots
-    int keep;             // 1: factors stored per system k, 0: per CTA slot (transient)
+    int keep;             // 1: factors stored per system k, 0: per system of this launch (slot k - k0)
     int* status;          // status[0] set to 1 on a zero / non-finite pivot
 };
 template <typename T> int band_pick_nb(int b, size_t smem_optin);
 template <typename T> size_t band_smem_for(int nb, int b);
 template <typename T> int band_occupancy(int nb, int b);
 template <typename T> cudaError_t band_factor_solve_launch(const BandArgs<T>& a, int nb, int grid, cudaStream_t st);
-template <typename T> cudaError_t band_solve_launch(const BandArgs<T>& a, int nb, int grid, cudaStream_t st);
+template <typename T> cudaError_t subst_launch(const BandArgs<T>& a, int k0, int nsys, bool fwd, cudaStream_t st);
 
 }  // namespace stfdm
 
@@ -132,6 +133,12 @@ struct st_fdm {
     double* ws_red = nullptr;     // reduction partials + scalars
     size_t ws_red_bytes = 0;
     int* ws_status = nullptr;     // device status flags
+    void* ws_kry = nullptr;       // GMRES basis V (m+1) and preconditioned directions Z (m), c128
+    size_t ws_kry_bytes = 0;
+    double2** kry_ptrs = nullptr; // device array of 2m+2 vector pointers: V_0..V_m, Z_0..Z_{m-1}, w
+    void* kry_small = nullptr;    // multi-dot partials and coefficient buffers
+    size_t kry_small_bytes = 0;
+    int kry_m = 0;
     int factors_valid = 0;        // ws_L holds the factors of all n_t systems (keep mode)
     int factors_prec = -1;
 };

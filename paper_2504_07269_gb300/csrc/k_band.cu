@@ -17,10 +17,9 @@
 //   * a panel (NB columns x (NB+b) rows) is copied to shared memory and factorised
 //     there; its L and L*D columns then drive a rank-NB update of the b x b trailing
 //     triangle of the window, register-tiled 8 rows x 2 columns per lane;
-//   * forward substitution L z = g is fused into the panel sweep, the columns of L
-//     (b entries each) and D are written out, and the backward substitution
-//     L^T w = D^{-1} z runs blocked from the end with warp reductions.
-// A second entry runs forward + backward substitution only, from stored factors.
+//   * forward substitution L z = g and y = D^{-1} z are fused into the panel sweep, and
+//     the columns of L (b entries each) and D are written out for the backward
+//     substitution L^T w = y (k_subst.cu), which streams them back in reverse order.
 #include <cuda_runtime.h>
 
 #include <cstdio>
@@ -62,21 +61,18 @@ __device__ __forceinline__ bool bad_pivot(C<T> d) {
 //   P  [NB][WR]  panel, column-major by panel column (L after factorisation)
 //   LD [NB][WR]  L * D of the panel
 //   zb [WR]      circular forward-substitution vector (rows c0 .. c0+WR-1)
-//   Lb [NB][NB]  intra-block factor entries for the backward substitution
-//   part[NB], dsh[NB]
 template <typename T, int NB>
-__device__ void band_factor_one(const BandArgs<T>& a, int k, char* smem) {
+__device__ void band_factor_one(const BandArgs<T>& a, int k, int ks, char* smem) {
     const int n = a.n, b = a.b, WR = b + NB, WB = b + 1;
     const int tid = threadIdx.x, nth = blockDim.x;
     const int lane = tid & 31, warp = tid >> 5, nwarps = nth >> 5;
+    (void)lane;
     C<T>* P = reinterpret_cast<C<T>*>(smem);
     C<T>* LD = P + NB * WR;
     C<T>* zb = LD + NB * WR;
-    C<T>* Lb = zb + WR;
-    C<T>* part = Lb + NB * NB;
     const C<T> s = a.shifts[k];
     C<T>* z = a.rhs + (size_t)k * n;
-    const size_t slot = a.keep ? (size_t)k : (size_t)blockIdx.x;
+    const size_t slot = a.keep ? (size_t)k : (size_t)ks;
     C<T>* Lk = a.L + slot * (size_t)n * b;
     C<T>* Dk = a.D + slot * (size_t)n;
     C<T>* W = a.win + (size_t)blockIdx.x * WR * WB;
@@ -202,142 +198,13 @@ __device__ void band_factor_one(const BandArgs<T>& a, int k, char* smem) {
         __syncthreads();
     }
 
-    // backward substitution L^T w = y (y = D^{-1} z is in z), blocks of NB rows from the end;
-    // zb holds w of the last WR rows solved (circular)
-    const int nblk = (n + NB - 1) / NB;
-    for (int bi = nblk - 1; bi >= 0; --bi) {
-        const int J = bi * NB;
-        const int nbk = min(NB, n - J);
-        // intra-block factor entries
-        for (int idx = tid; idx < NB * NB; idx += nth) {
-            int q = idx / NB, o = idx - q * NB;  // L(J+q+o, J+q) for 1 <= o < nbk - q
-            Lb[idx] = (o >= 1 && q + o < nbk) ? Lk[(size_t)(J + q) * b + (o - 1)] : mk<T>(0, 0);
-        }
-        // partial sums over already solved rows j + o >= J + nbk
-        for (int q = warp; q < nbk; q += nwarps) {
-            const int j = J + q;
-            C<T> acc = mk<T>(0, 0);
-            const int omin = nbk - q;                 // j + omin = J + nbk
-            const int omax = min(b, n - 1 - j);
-            for (int o = omin + lane; o <= omax; o += 32)
-                cfma<T>(acc, Lk[(size_t)j * b + (o - 1)], zb[(j + o) % WR]);
-#pragma unroll
-            for (int off = 16; off > 0; off >>= 1) {
-                acc.x += __shfl_down_sync(0xffffffffu, acc.x, off);
-                acc.y += __shfl_down_sync(0xffffffffu, acc.y, off);
-            }
-            if (lane == 0) part[q] = acc;
-        }
-        __syncthreads();
-        if (tid == 0) {
-            for (int q = nbk - 1; q >= 0; --q) {
-                C<T> acc = csub<T>(z[J + q], part[q]);
-                for (int o = 1; q + o < nbk; ++o) cfms<T>(acc, Lb[q * NB + o], zb[(J + q + o) % WR]);
-                zb[(J + q) % WR] = acc;
-                z[J + q] = acc;
-            }
-        }
-        __syncthreads();
-    }
-}
-
-// Forward + backward substitution with stored factors (keep mode).
-template <typename T, int NB>
-__device__ void band_solve_one(const BandArgs<T>& a, int k, char* smem) {
-    const int n = a.n, b = a.b, WR = b + NB;
-    const int tid = threadIdx.x, nth = blockDim.x;
-    const int lane = tid & 31, warp = tid >> 5, nwarps = nth >> 5;
-    C<T>* zb = reinterpret_cast<C<T>*>(smem);
-    C<T>* Lb = zb + WR;
-    C<T>* part = Lb + NB * NB;
-    C<T>* z = a.rhs + (size_t)k * n;
-    const C<T>* Lk = a.L + (size_t)k * n * b;
-    const C<T>* Dk = a.D + (size_t)k * n;
-    const int r0n = min(WR, n);
-    for (int i = tid; i < r0n; i += nth) zb[i % WR] = z[i];
-    __syncthreads();
-    // forward, column oriented: after the block's own triangle, update the next b rows
-    for (int J = 0; J < n; J += NB) {
-        const int nbk = min(NB, n - J);
-        for (int idx = tid; idx < NB * NB; idx += nth) {
-            int q = idx / NB, o = idx - q * NB;
-            Lb[idx] = (o >= 1 && q + o < nbk) ? Lk[(size_t)(J + q) * b + (o - 1)] : mk<T>(0, 0);
-        }
-        __syncthreads();
-        if (tid == 0) {
-            for (int q = 0; q < nbk; ++q) {
-                C<T> acc = zb[(J + q) % WR];
-                for (int q1 = 0; q1 < q; ++q1) cfms<T>(acc, Lb[q1 * NB + (q - q1)], zb[(J + q1) % WR]);
-                zb[(J + q) % WR] = acc;
-            }
-        }
-        __syncthreads();
-        const int rmax = min(J + nbk + b, n);    // rows J+nbk .. rmax-1 receive updates
-        for (int i = J + nbk + tid; i < rmax; i += nth) {
-            C<T> acc = zb[i % WR];
-            for (int q = 0; q < nbk; ++q) {
-                int o = i - (J + q);
-                if (o <= b) cfms<T>(acc, Lk[(size_t)(J + q) * b + (o - 1)], zb[(J + q) % WR]);
-            }
-            zb[i % WR] = acc;
-        }
-        for (int q = tid; q < nbk; q += nth) z[J + q] = cmul<T>(zb[(J + q) % WR], cinv<T>(Dk[J + q]));
-        __syncthreads();
-        // rows entering the circular buffer
-        const int i0 = J + WR;
-        for (int x = tid; x < nbk && i0 + x < n; x += nth) zb[(i0 + x) % WR] = z[i0 + x];
-        __syncthreads();
-    }
-    // backward (same as in the factor kernel)
-    const int nblk = (n + NB - 1) / NB;
-    for (int bi = nblk - 1; bi >= 0; --bi) {
-        const int J = bi * NB;
-        const int nbk = min(NB, n - J);
-        for (int idx = tid; idx < NB * NB; idx += nth) {
-            int q = idx / NB, o = idx - q * NB;
-            Lb[idx] = (o >= 1 && q + o < nbk) ? Lk[(size_t)(J + q) * b + (o - 1)] : mk<T>(0, 0);
-        }
-        for (int q = warp; q < nbk; q += nwarps) {
-            const int j = J + q;
-            C<T> acc = mk<T>(0, 0);
-            const int omin = nbk - q;
-            const int omax = min(b, n - 1 - j);
-            for (int o = omin + lane; o <= omax; o += 32)
-                cfma<T>(acc, Lk[(size_t)j * b + (o - 1)], zb[(j + o) % WR]);
-#pragma unroll
-            for (int off = 16; off > 0; off >>= 1) {
-                acc.x += __shfl_down_sync(0xffffffffu, acc.x, off);
-                acc.y += __shfl_down_sync(0xffffffffu, acc.y, off);
-            }
-            if (lane == 0) part[q] = acc;
-        }
-        __syncthreads();
-        if (tid == 0) {
-            for (int q = nbk - 1; q >= 0; --q) {
-                C<T> acc = csub<T>(z[J + q], part[q]);
-                for (int o = 1; q + o < nbk; ++o) cfms<T>(acc, Lb[q * NB + o], zb[(J + q + o) % WR]);
-                zb[(J + q) % WR] = acc;
-                z[J + q] = acc;
-            }
-        }
-        __syncthreads();
-    }
 }
 
 template <typename T, int NB>
 __global__ void __launch_bounds__(256) k_band_factor_solve(BandArgs<T> a) {
     extern __shared__ __align__(16) char smem[];
-    for (int k = blockIdx.x; k < a.n_sys; k += gridDim.x) {
-        band_factor_one<T, NB>(a, k, smem);
-        __syncthreads();
-    }
-}
-
-template <typename T, int NB>
-__global__ void __launch_bounds__(256) k_band_solve(BandArgs<T> a) {
-    extern __shared__ __align__(16) char smem[];
-    for (int k = blockIdx.x; k < a.n_sys; k += gridDim.x) {
-        band_solve_one<T, NB>(a, k, smem);
+    for (int ks = blockIdx.x; ks < a.n_sys; ks += gridDim.x) {
+        band_factor_one<T, NB>(a, a.k0 + ks, ks, smem);
         __syncthreads();
     }
 }
@@ -345,14 +212,8 @@ __global__ void __launch_bounds__(256) k_band_solve(BandArgs<T> a) {
 template <typename T, int NB>
 size_t band_factor_smem(int b) {
     const int WR = b + NB;
-    return sizeof(C<T>) * ((size_t)2 * NB * WR + WR + NB * NB + NB);
+    return sizeof(C<T>) * ((size_t)2 * NB * WR + WR);
 }
-template <typename T, int NB>
-size_t band_solve_smem(int b) {
-    const int WR = b + NB;
-    return sizeof(C<T>) * ((size_t)WR + NB * NB + NB);
-}
-
 // ------------------------------------------------------------------ host launchers
 template <typename T>
 struct BandPlan {
@@ -369,15 +230,6 @@ static cudaError_t launch_factor_nb(const BandArgs<T>& a, int grid, cudaStream_t
     k_band_factor_solve<T, NB><<<grid, 256, smem, st>>>(a);
     return cudaGetLastError();
 }
-template <typename T, int NB>
-static cudaError_t launch_solve_nb(const BandArgs<T>& a, int grid, cudaStream_t st) {
-    size_t smem = band_solve_smem<T, NB>(a.b);
-    cudaError_t e = cudaFuncSetAttribute(k_band_solve<T, NB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    k_band_solve<T, NB><<<grid, 256, smem, st>>>(a);
-    return cudaGetLastError();
-}
-
 // Chooses the panel width that fits the shared-memory budget.
 template <typename T>
 int band_pick_nb(int b, size_t smem_optin) {
@@ -396,12 +248,6 @@ cudaError_t band_factor_solve_launch(const BandArgs<T>& a, int nb, int grid, cud
     if (nb == 16) return launch_factor_nb<T, 16>(a, grid, st);
     return launch_factor_nb<T, 8>(a, grid, st);
 }
-template <typename T>
-cudaError_t band_solve_launch(const BandArgs<T>& a, int nb, int grid, cudaStream_t st) {
-    if (nb == 16) return launch_solve_nb<T, 16>(a, grid, st);
-    return launch_solve_nb<T, 8>(a, grid, st);
-}
-
 template <typename T>
 int band_occupancy(int nb, int b) {
     int occ = 0;
@@ -425,7 +271,5 @@ template size_t band_smem_for<float>(int, int);
 template size_t band_smem_for<double>(int, int);
 template cudaError_t band_factor_solve_launch<float>(const BandArgs<float>&, int, int, cudaStream_t);
 template cudaError_t band_factor_solve_launch<double>(const BandArgs<double>&, int, int, cudaStream_t);
-template cudaError_t band_solve_launch<float>(const BandArgs<float>&, int, int, cudaStream_t);
-template cudaError_t band_solve_launch<double>(const BandArgs<double>&, int, int, cudaStream_t);
 
 }  // namespace stfdm

@@ -58,7 +58,7 @@ struct ResArgs {
     const double* Mb;   // n_t x 5 band of M_t
     const double* Bb;   // n_t x 5 band of B_t (or B_t^T)
     double bsign;       // +1: K;  -1 with B_t^T: K^H
-    const double2* F;
+    const double2* F;      // right-hand side, or NULL: then R = K U (operator apply)
     const double2* apsi0;  // A_x psi0 or NULL
     const double* m_t;
     const double2* U;      // current iterate or NULL (= 0)
@@ -115,7 +115,7 @@ __global__ void __launch_bounds__(256) k_residual(ResArgs a) {
                 Q[d] = Q[d + 1];
             }
             load_row_shift(l + 2, P[4], Q[4]);
-            const double2 f = a.F[(size_t)l * a.n_x + x];
+            const double2 f = a.F ? a.F[(size_t)l * a.n_x + x] : make_double2(0, 0);
             const double ml = a.m_t[l];
             double2 ft = make_double2(f.x - ml * ap.x, f.y - ml * ap.y);
             double2 kv = make_double2(0, 0);
@@ -127,7 +127,8 @@ __global__ void __launch_bounds__(256) k_residual(ResArgs a) {
                 kv.x += -bc * P[d].y + mc * Q[d].x;
                 kv.y += bc * P[d].x + mc * Q[d].y;
             }
-            double2 r = make_double2(ft.x - kv.x, ft.y - kv.y);
+            // residual F~ - K U, or the plain product K U when no right-hand side is given
+            double2 r = a.F ? make_double2(ft.x - kv.x, ft.y - kv.y) : kv;
             if (a.R) a.R[(size_t)l * a.n_x + x] = r;
             rr += r.x * r.x + r.y * r.y;
             ff += ft.x * ft.x + ft.y * ft.y;

@@ -9,6 +9,7 @@
 //   * r1_u, r1_v: subtract the rank-one lifting term u[l] v[x] with u = Y_t m_t,
 //     v = A_x psi0 (Y_t (F - m_t (x) A_x psi0) = Y_t F - (Y_t m_t) (x) A_x psi0);
 //   * add_row: add psi0 to every row (psi = psi_hat + psi0);
+//   * out_scale: device scalar multiplying the product (undoes the input scaling);
 //   * accumulate: out += out_scale * product (refinement update psi_hat += delta).
 #include <cuda_runtime.h>
 
@@ -70,7 +71,7 @@ __global__ void __launch_bounds__(256) k_xform_simt(XformArgs<TA, TB, TC> a) {
         __syncthreads();
     }
     double osc = 1.0;
-    if (a.accumulate && a.out_scale) osc = *a.out_scale;
+    if (a.out_scale) osc = *a.out_scale;
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
         const int gm = m0 + ty + 16 * i;
@@ -96,7 +97,7 @@ __global__ void __launch_bounds__(256) k_xform_simt(XformArgs<TA, TB, TC> a) {
                 C<TC> o = *out;
                 *out = mk<TC>((TC)((double)o.x + osc * vx), (TC)((double)o.y + osc * vy));
             } else {
-                *out = mk<TC>((TC)vx, (TC)vy);
+                *out = mk<TC>((TC)(osc * vx), (TC)(osc * vy));
             }
         }
     }

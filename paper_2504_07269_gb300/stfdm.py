@@ -85,14 +85,26 @@ def _check_vec(h: FdmHandle, t, dtype, name):
         raise ValueError(f"{name}: expected a contiguous CUDA {dtype} tensor of shape {(h.n_x,)}")
 
 
+def _check_with_info(status, where, info):
+    """Raise on error; the exception carries the solve info (filled on NOT_CONVERGED too)."""
+    if status != _lib.ST_OK:
+        err = _lib.StfdmError(status, where)
+        err.info = _info_dict(info) if info is not None else None
+        raise err
+
+
 def _dtype(precision):
     return torch.complex64 if precision == "fp32" else torch.complex128
 
 
-def _opts(precision="fp64", tol=0.0, max_sweeps=0, keep_factors=-1, fixed_sweeps=0):
+REFINE = {"gmres": _lib.ST_REFINE_GMRES, "classic": _lib.ST_REFINE_CLASSIC}
+
+
+def _opts(precision="fp64", tol=0.0, max_sweeps=0, keep_factors=-1, fixed_sweeps=0, method="gmres"):
     if precision not in PREC:
         raise ValueError(f"unknown precision {precision!r}")
-    return _lib.st_solve_opts(PREC[precision], float(tol), int(max_sweeps), int(keep_factors), int(fixed_sweeps))
+    return _lib.st_solve_opts(PREC[precision], float(tol), int(max_sweeps), int(keep_factors), int(fixed_sweeps),
+                              REFINE[method])
 
 
 def _info_dict(info: _lib.st_solve_info):
@@ -157,17 +169,18 @@ def st_fdm_setup(t: TimeHandle, s: SpaceHandle, kappa_max: float = 0.0, device: 
 
 # ------------------------------------------------------------------ solves
 def st_fdm_solve(h: FdmHandle, F, psi0=None, psi=None, precision="fp64", tol=0.0, max_sweeps=0,
-                 keep_factors=-1, fixed_sweeps=0, stream=None, want_info=True):
+                 keep_factors=-1, fixed_sweeps=0, stream=None, want_info=True, method="gmres"):
     dt = _dtype(precision)
     _check_st(h, F, dt, "F")
     _check_vec(h, psi0, dt, "psi0")
     if psi is None:
         psi = torch.empty_like(F)
     _check_st(h, psi, dt, "psi")
-    opts = _opts(precision, tol, max_sweeps, keep_factors, fixed_sweeps)
+    opts = _opts(precision, tol, max_sweeps, keep_factors, fixed_sweeps, method)
     info = _lib.st_solve_info()
-    check(lib().st_fdm_solve(h.ptr, _ptr(F), _ptr(psi0), _ptr(psi), ctypes.byref(opts),
-                             ctypes.byref(info) if want_info else None, _stream(stream)), "st_fdm_solve")
+    st = lib().st_fdm_solve(h.ptr, _ptr(F), _ptr(psi0), _ptr(psi), ctypes.byref(opts),
+                            ctypes.byref(info) if want_info else None, _stream(stream))
+    _check_with_info(st, "st_fdm_solve", info if want_info else None)
     return psi, (_info_dict(info) if want_info else None)
 
 
@@ -183,16 +196,17 @@ def st_residual(h: FdmHandle, F, psi0, psi, R=None, want_norm=True, stream=None)
 
 
 def st_adjoint_solve(h: FdmHandle, G, lam=None, precision="fp64", tol=0.0, max_sweeps=0, keep_factors=-1,
-                     fixed_sweeps=0, stream=None, want_info=True):
+                     fixed_sweeps=0, stream=None, want_info=True, method="gmres"):
     dt = _dtype(precision)
     _check_st(h, G, dt, "G")
     if lam is None:
         lam = torch.empty_like(G)
     _check_st(h, lam, dt, "lambda")
-    opts = _opts(precision, tol, max_sweeps, keep_factors, fixed_sweeps)
+    opts = _opts(precision, tol, max_sweeps, keep_factors, fixed_sweeps, method)
     info = _lib.st_solve_info()
-    check(lib().st_adjoint_solve(h.ptr, _ptr(G), _ptr(lam), ctypes.byref(opts),
-                                 ctypes.byref(info) if want_info else None, _stream(stream)), "st_adjoint_solve")
+    st = lib().st_adjoint_solve(h.ptr, _ptr(G), _ptr(lam), ctypes.byref(opts),
+                                ctypes.byref(info) if want_info else None, _stream(stream))
+    _check_with_info(st, "st_adjoint_solve", info if want_info else None)
     return lam, (_info_dict(info) if want_info else None)
 
 
@@ -208,7 +222,7 @@ def st_adjoint_lift(h: FdmHandle, grad_psi, grad_F, grad_psi0=None, stream=None)
 
 
 def st_fdm_solve_batched(hs, Fs, psi0s=None, psis=None, precision="fp64", tol=0.0, max_sweeps=0,
-                         keep_factors=-1, fixed_sweeps=0, stream=None, want_info=True):
+                         keep_factors=-1, fixed_sweeps=0, stream=None, want_info=True, method="gmres"):
     n = len(hs)
     dt = _dtype(precision)
     if psis is None:
@@ -223,7 +237,7 @@ def st_fdm_solve_batched(hs, Fs, psi0s=None, psis=None, precision="fp64", tol=0.
     Fp = (ctypes.c_void_p * n)(*[F.data_ptr() for F in Fs])
     Pp = (ctypes.c_void_p * n)(*[p.data_ptr() for p in psis])
     P0 = (ctypes.c_void_p * n)(*[(p.data_ptr() if p is not None else None) for p in psi0s]) if psi0s else None
-    opts = _opts(precision, tol, max_sweeps, keep_factors, fixed_sweeps)
+    opts = _opts(precision, tol, max_sweeps, keep_factors, fixed_sweeps, method)
     infos = (_lib.st_solve_info * n)()
     check(lib().st_fdm_solve_batched(H, n, Fp, P0, Pp, ctypes.byref(opts), infos if want_info else None,
                                      _stream(stream)), "st_fdm_solve_batched")
