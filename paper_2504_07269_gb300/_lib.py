@@ -77,6 +77,7 @@ SIGNATURES = {
     "st_time_transform": (c_int, [c_void_p, c_int, c_int, c_void_p, c_void_p, c_void_p]),
     "st_spatial_solve": (c_int, [c_void_p, c_int, c_void_p, c_void_p, c_void_p]),
     "st_load_nodal": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p]),
+    "st_residual_noalloc": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]),
     "st_destroy_time": (None, [c_void_p]),
     "st_destroy_space": (None, [c_void_p]),
     "st_destroy_fdm": (None, [c_void_p]),

@@ -275,6 +275,20 @@ def st_load_nodal(h: FdmHandle, f_nodal, F=None, stream=None):
     return F
 
 
+def st_residual_noalloc(h: FdmHandle, F, psi0, psi, R, norms, stream=None):
+    """Allocation-free residual: writes R (or nothing if R is None) and norms[0:2] =
+    (||R||^2, ||F~||^2) into caller-provided device tensors; never synchronises."""
+    _check_st(h, F, torch.complex128, "F")
+    _check_st(h, psi, torch.complex128, "psi")
+    _check_vec(h, psi0, torch.complex128, "psi0")
+    _check_st(h, R, torch.complex128, "R")
+    if not norms.is_cuda or norms.dtype != torch.float64 or norms.numel() < 2 or not norms.is_contiguous():
+        raise ValueError("norms: expected a contiguous CUDA float64 tensor with 2 entries")
+    check(lib().st_residual_noalloc(h.ptr, _ptr(F), _ptr(psi0), _ptr(psi), _ptr(R), _ptr(norms), _stream(stream)),
+          "st_residual_noalloc")
+    return norms
+
+
 def setup_problem(n_squares: int, p_t: int, t_nodes, Lx: float = 1.0, Ly: float = 1.0, **kw) -> FdmHandle:
     """assemble_time + assemble_space + fdm_setup in one call."""
     t = st_assemble_time(p_t, t_nodes)
