@@ -165,6 +165,7 @@ def config_problem(name: str) -> Problem:
     c2check   64x64 squares, P1 time, 128 uniform elements, T=1 (508,032)
     c3        384x384 squares, P2 time, 512 uniform elements, T=2 (150,209,536)
     c4        128x128 squares, P1 time, 256 uniform elements, T=1 (4,129,024)
+    c2small   256x256 squares, P1 time, 16 uniform elements, T=1/32 (profiling case)
     paperJ    paper's level-J mesh: (32 2^J)^2 squares, P1, 64 2^J elements, T=5
     """
     if name == "c1":
@@ -177,6 +178,9 @@ def config_problem(name: str) -> Problem:
         return Problem(384, 2, uniform_time_nodes(512, 2.0), name=name, seed=3)
     if name == "c4":
         return Problem(128, 1, uniform_time_nodes(256, 1.0), name=name, seed=4)
+    if name == "c2small":
+        # the 256x256 spatial band of c2 with 16 time elements: a small case for profiling
+        return Problem(256, 1, uniform_time_nodes(16, 1.0 / 32), name=name, seed=2)
     if name.startswith("paperJ"):
         J = int(name[6:])
         return Problem(32 * 2 ** J, 1, uniform_time_nodes(64 * 2 ** J, 5.0), name=name, seed=0)
