@@ -190,7 +190,8 @@ st_status band_run(st_fdm* h, C<T>* G, int mode, cudaStream_t st) {
     a.shifts = shifts_of<T>(h);
     a.rhs = G;
     a.status = h->ws_status;
-    const size_t WR = (size_t)b + nb;
+    const int nbw = nb == 64 ? 32 : (nb < 0 ? -nb : nb);   // panel width of the selected kernel
+    const size_t WR = (size_t)b + nbw;
     if (mode == 2) {
         if (!h->factors_valid || h->factors_prec != (int)sizeof(T))
             return fail(ST_ERR_ARG, "spatial solve: no stored factors");

@@ -93,10 +93,19 @@ struct BandArgs {
     int keep;             // 1: factors stored per system k, 0: per system of this launch (slot k - k0)
     int* status;          // status[0] set to 1 on a zero / non-finite pivot
 };
+// panel width code: the panel width (32/16/8), negative for the unstaged complex64 kernel, 0 = too wide
 template <typename T> int band_pick_nb(int b, size_t smem_optin);
 template <typename T> size_t band_smem_for(int nb, int b);
 template <typename T> int band_occupancy(int nb, int b);
 template <typename T> cudaError_t band_factor_solve_launch(const BandArgs<T>& a, int nb, int grid, cudaStream_t st);
+template <> int band_pick_nb<float>(int b, size_t smem_optin);
+template <> int band_pick_nb<double>(int b, size_t smem_optin);
+template <> size_t band_smem_for<float>(int nb, int b);
+template <> size_t band_smem_for<double>(int nb, int b);
+template <> int band_occupancy<float>(int nb, int b);
+template <> int band_occupancy<double>(int nb, int b);
+template <> cudaError_t band_factor_solve_launch<float>(const BandArgs<float>& a, int nb, int grid, cudaStream_t st);
+template <> cudaError_t band_factor_solve_launch<double>(const BandArgs<double>& a, int nb, int grid, cudaStream_t st);
 template <typename T> cudaError_t subst_launch(const BandArgs<T>& a, int k0, int nsys, bool fwd, cudaStream_t st);
 
 }  // namespace stfdm

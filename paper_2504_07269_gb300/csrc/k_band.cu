@@ -10,7 +10,8 @@
 // Band structure: interior nodes lexicographic, x1 fastest, m per row; C_k is a 7-point
 // stencil with half bandwidth b = m + 1 and the factor fills the whole band.
 //
-// Kernel design (one CTA per system at a time, persistent over systems):
+// Generic kernel (complex128, and complex64 when the blocked one does not fit); one CTA per
+// system at a time, persistent over systems:
 //   * right-looking blocked band LDL^T with panels of NB columns;
 //   * the active window -- rows c0 .. c0+NB+b-1 of the band, stored by row as offsets
 //     o = i - j in [0, b] -- lives in a per-CTA global scratch buffer (row-circular);
@@ -154,7 +155,7 @@ __device__ void band_factor_one(const BandArgs<T>& a, int k, int ks, char* smem)
             zb[(c0 + r) % WR] = acc;
         }
         if (tid < nbk) z[c0 + tid] = cmul<T>(zb[(c0 + tid) % WR], cinv<T>(P[tid * WR + tid]));
-        // 6. trailing update of the b x b triangle: W(r, r2) -= sum_q L(r, q) d_q L(r2, q)
+        // 6. trailing update of the b x b triangle: W(r, r2) -= sum_q L(r, q) d_q L(r2, q);
         {
             const int R6 = rows_p - nbk;
             const int ngroups = (R6 + 7) >> 3;
@@ -211,6 +212,255 @@ __device__ void band_factor_one(const BandArgs<T>& a, int k, int ks, char* smem)
     }
 }
 
+// ------------------------------------------------------------------ complex64, blocked panel
+// Panel of 32 columns, two CTAs of 256 threads per SM (one CTA's serial panel work overlaps
+// the other's trailing update).  Warp 0 factors the 32 x 32 top block in registers (lane =
+// row; the pivot and L entries travel by shuffles) and publishes U = D L11^T; every row r
+// below then solves l_r U = p_r by a register-resident forward substitution (no barriers).
+// The trailing update uses an 8 x 2 register tile per lane with L D formed on the fly and
+// skips 32-column sub-blocks that lie entirely above the diagonal.
+constexpr int V4_THREADS = 256;
+constexpr int V4_NB = 32;
+
+__device__ __forceinline__ float2 shfl2(float2 v, int src) {
+    return make_float2(__shfl_sync(0xffffffffu, v.x, src), __shfl_sync(0xffffffffu, v.y, src));
+}
+
+__device__ void band_factor_v4(const BandArgs<float>& a, int k, int ks, char* smem) {
+    using T = float;
+    constexpr int NB = V4_NB;
+    const int n = a.n, b = a.b, m = a.m, WR = b + NB, WB = b + 1;
+    const int tid = threadIdx.x, nth = blockDim.x;
+    const int lane = tid & 31, warp = tid >> 5, nwarps = nth >> 5;
+    float2* P = reinterpret_cast<float2*>(smem);     // [NB][WR]  panel -> L (pivots on the diagonal)
+    float2* Us = P + NB * WR;                          // [NB][NB]  U[q'][q] = d_q' L(q, q') for q' < q
+    float2* dinv = Us + NB * NB;                       // [NB]
+    float2* zb = dinv + NB;                            // [WR]
+    const float2 s = a.shifts[k];
+    float2* z = a.rhs + (size_t)k * n;
+    const size_t slot = a.keep ? (size_t)k : (size_t)ks;
+    float2* Lk = a.L + slot * (size_t)n * b;
+    float2* Dk = a.D + slot * (size_t)n;
+    float2* W = a.win + (size_t)blockIdx.x * WR * WB;
+    // a new band row i (one warp): zero except the stencil offsets 0, 1, m, m + 1
+    auto fill_row = [&](int i) {
+        float2* row = W + (size_t)(i % WR) * WB;
+        const int xi = i % m, yj = i / m;
+        const float2 e0 = mk<T>(a.Mc + s.x * a.Ac, s.y * a.Ac);
+        const float2 e1 = (xi >= 1) ? mk<T>(a.Mw + s.x * a.Aw, s.y * a.Aw) : mk<T>(0, 0);
+        const float2 em = (yj >= 1) ? mk<T>(a.Ms + s.x * a.As, s.y * a.As) : mk<T>(0, 0);
+        const float2 ed = (xi >= 1 && yj >= 1) ? mk<T>(a.Md + s.x * a.Ad, s.y * a.Ad) : mk<T>(0, 0);
+        for (int o = lane; o < WB; o += 32) {
+            float2 v = mk<T>(0, 0);
+            if (o <= i) {
+                if (o == 0) v = e0;
+                else if (o == m) v = em;
+                else if (o == 1) v = e1;
+                else if (o == m + 1) v = ed;
+            }
+            row[o] = v;
+        }
+    };
+
+    const int r0n = min(WR, n);
+    for (int i = warp; i < r0n; i += nwarps) fill_row(i);
+    for (int i = tid; i < r0n; i += nth) zb[i % WR] = z[i];
+    __syncthreads();
+
+    for (int c0 = 0; c0 < n; c0 += NB) {
+        const int nbk = min(NB, n - c0);
+        const int rows_p = min(WR, n - c0);
+        const int rbase = c0 % WR;
+        // 1. panel to shared memory: each thread reads whole rows (contiguous offsets), loads batched
+        for (int r = tid; r < WR; r += nth) {
+            int sl = rbase + r;
+            if (sl >= WR) sl -= WR;
+            const float2* wrow = W + (size_t)sl * WB;
+#pragma unroll
+            for (int h = 0; h < NB; h += 16) {
+                float2 v[16];
+#pragma unroll
+                for (int u = 0; u < 16; ++u) {
+                    const int q = h + u;
+                    v[u] = (q < nbk && r >= q && r < rows_p && r - q <= b) ? wrow[r - q] : mk<T>(0, 0);
+                }
+#pragma unroll
+                for (int u = 0; u < 16; ++u) P[(h + u) * WR + r] = v[u];
+            }
+        }
+        __syncthreads();
+        // 2a. LDL^T of the 32 x 32 top block by the whole CTA: in step q, thread t updates
+        //     row r = t / 8 at columns q2 = q + 1 + t % 8 (+ 8, + 16, ...) <= r (unscaled form)
+        {
+            const int r = tid >> 3, g = tid & 7;
+            for (int q = 0; q < nbk; ++q) {
+                float2 d = P[q * WR + q];
+                if (bad_pivot<T>(d)) d = mk<T>(1e-30f, 0);
+                const float2 di = cinv<T>(d);
+                if (r > q && r < nbk) {
+                    const float2 x = P[q * WR + r];
+                    for (int q2 = q + 1 + g; q2 <= r; q2 += 8) cfms<T>(P[q2 * WR + r], x, cmul<T>(P[q * WR + q2], di));
+                }
+                __syncthreads();
+            }
+        }
+        // pivots, 1/d, scaled L11 and U[q'][q] = d_q' L(q, q')
+        if (tid < nbk) {
+            float2 d = P[tid * WR + tid];
+            if (bad_pivot<T>(d)) {
+                atomicExch(a.status, 1);
+                d = mk<T>(1e-30f, 0);
+                P[tid * WR + tid] = d;
+            }
+            dinv[tid] = cinv<T>(d);
+        }
+        __syncthreads();
+        for (int idx = tid; idx < NB * NB; idx += nth) {
+            const int q = idx / NB, r = idx % NB;   // entry (r, q) of the top block
+            float2 u = mk<T>(0, 0);
+            if (q < r && r < nbk) {
+                const float2 lrq = cmul<T>(P[q * WR + r], dinv[q]);
+                u = cmul<T>(P[q * WR + q], lrq);       // d_q L(r, q) = unscaled entry
+                P[q * WR + r] = lrq;
+            }
+            Us[q * NB + r] = u;                        // U[q][r] = d_q L(r, q)
+        }
+        __syncthreads();
+        // 2b. rows below the top block: l_r[q] = (p_r[q] - sum_{q'<q} l_r[q'] U[q'][q]) / d_q
+        for (int r = nbk + tid; r < rows_p; r += nth) {
+            float2 l[NB];
+#pragma unroll
+            for (int q = 0; q < NB; ++q) {
+                float2 acc = P[q * WR + r];
+#pragma unroll
+                for (int q1 = 0; q1 < q; ++q1) cfms<T>(acc, l[q1], Us[q1 * NB + q]);
+                l[q] = (q < nbk) ? cmul<T>(acc, dinv[q]) : mk<T>(0, 0);
+            }
+#pragma unroll
+            for (int q = 0; q < NB; ++q)
+                if (q < nbk) P[q * WR + r] = l[q];
+        }
+        __syncthreads();
+        // 3. warp 0: forward substitution inside the panel; the others write L and D out
+        if (warp == 0) {
+            const int q = lane;
+            int sq = rbase + q;
+            if (sq >= WR) sq -= WR;
+            float2 zq = (q < nbk) ? zb[sq] : mk<T>(0, 0);
+            for (int q1 = 0; q1 < nbk; ++q1) {
+                const float2 z1 = shfl2(zq, q1);
+                if (q > q1 && q < nbk) cfms<T>(zq, P[q1 * WR + q], z1);
+            }
+            if (q < nbk) zb[sq] = zq;
+        } else {
+            for (int q = 0; q < nbk; ++q)
+                for (int o = tid - 31; o <= b; o += nth - 32) {
+                    const int r = q + o;
+                    Lk[(size_t)(c0 + q) * b + (o - 1)] = (r < rows_p) ? P[q * WR + r] : mk<T>(0, 0);
+                }
+            if (tid - 32 < nbk) Dk[c0 + tid - 32] = P[(tid - 32) * WR + (tid - 32)];
+        }
+        __syncthreads();
+        // 4. forward substitution below the panel; y = z / d of the panel rows out
+        for (int r = nbk + tid; r < rows_p; r += nth) {
+            int sl = rbase + r;
+            if (sl >= WR) sl -= WR;
+            float2 acc = zb[sl];
+            int sq = rbase;
+            for (int q = 0; q < nbk; ++q) {
+                cfms<T>(acc, P[q * WR + r], zb[sq]);
+                if (++sq == WR) sq = 0;
+            }
+            zb[sl] = acc;
+        }
+        if (tid < nbk) {
+            int sq = rbase + tid;
+            if (sq >= WR) sq -= WR;
+            z[c0 + tid] = cmul<T>(zb[sq], dinv[tid]);
+        }
+        // 5. trailing update, items of 8 rows x 64 columns, 2 columns per lane
+        {
+            const int R6 = rows_p - nbk;
+            const int ngroups = (R6 + 7) >> 3;
+            for (int rg = warp; rg < ngroups; rg += nwarps) {
+                const int rr0 = rg * 8;
+                const int nseg = (rr0 + 7) / 64 + 1;
+                const int jmax = min(7, WR - 1 - nbk - rr0);
+                size_t rowb[8];
+#pragma unroll
+                for (int j = 0; j < 8; ++j) {
+                    int sl = rbase + nbk + rr0 + j;
+                    while (sl >= WR) sl -= WR;
+                    rowb[j] = (size_t)sl * WB;
+                }
+                for (int cs = 0; cs < nseg; ++cs) {
+                    const int cc0 = cs * 64 + lane, cc1 = cc0 + 32;
+                    const bool act1 = (cs * 64 + 32) <= (rr0 + 7);   // second sub-block touches the triangle
+                    float2 acc[8][2];
+#pragma unroll
+                    for (int j = 0; j < 8; ++j) {
+                        const int rr = rr0 + j;
+                        acc[j][0] = (rr < R6 && cc0 <= rr) ? W[rowb[j] + (rr - cc0)] : mk<T>(0, 0);
+                        acc[j][1] = (act1 && rr < R6 && cc1 <= rr) ? W[rowb[j] + (rr - cc1)] : mk<T>(0, 0);
+                    }
+                    const int ci0 = min(nbk + cc0, WR - 1), ci1 = min(nbk + cc1, WR - 1);
+                    if (act1) {
+#pragma unroll 2
+                        for (int q = 0; q < nbk; ++q) {
+                            const float2 dq = P[q * WR + q];
+                            const float2 a0 = cmul<T>(P[q * WR + ci0], dq);
+                            const float2 a1 = cmul<T>(P[q * WR + ci1], dq);
+                            const float2* prow = P + q * WR + nbk + rr0;
+#pragma unroll
+                            for (int j = 0; j < 8; ++j) {
+                                const float2 pv = prow[min(j, jmax)];
+                                cfms<T>(acc[j][0], pv, a0);
+                                cfms<T>(acc[j][1], pv, a1);
+                            }
+                        }
+                    } else {
+#pragma unroll 2
+                        for (int q = 0; q < nbk; ++q) {
+                            const float2 a0 = cmul<T>(P[q * WR + ci0], P[q * WR + q]);
+                            const float2* prow = P + q * WR + nbk + rr0;
+#pragma unroll
+                            for (int j = 0; j < 8; ++j) cfms<T>(acc[j][0], prow[min(j, jmax)], a0);
+                        }
+                    }
+#pragma unroll
+                    for (int j = 0; j < 8; ++j) {
+                        const int rr = rr0 + j;
+                        if (rr < R6 && cc0 <= rr) W[rowb[j] + (rr - cc0)] = acc[j][0];
+                        if (act1 && rr < R6 && cc1 <= rr) W[rowb[j] + (rr - cc1)] = acc[j][1];
+                    }
+                }
+            }
+        }
+        __syncthreads();
+        // 6. rows entering the window take the freed slots of the panel rows
+        {
+            const int i0 = c0 + WR;
+            const int cnt = min(nbk, n - i0);
+            for (int x = warp; x < cnt; x += nwarps) fill_row(i0 + x);
+            for (int x = tid; x < cnt; x += nth) zb[(i0 + x) % WR] = z[i0 + x];
+        }
+        __syncthreads();
+    }
+}
+
+__global__ void __launch_bounds__(V4_THREADS, 2) k_band_factor_v4(BandArgs<float> a) {
+    extern __shared__ __align__(16) char smem[];
+    for (int ks = blockIdx.x; ks < a.n_sys; ks += gridDim.x) {
+        band_factor_v4(a, a.k0 + ks, ks, smem);
+        __syncthreads();
+    }
+}
+
+size_t band_factor_v4_smem(int b) {
+    const int WR = b + V4_NB;
+    return sizeof(float2) * ((size_t)V4_NB * WR + V4_NB * V4_NB + V4_NB + WR);
+}
+
 template <typename T, int NB>
 __global__ void __launch_bounds__(256, 2) k_band_factor_solve(BandArgs<T> a) {
     extern __shared__ __align__(16) char smem[];
@@ -226,12 +476,6 @@ size_t band_factor_smem(int b) {
     return sizeof(C<T>) * ((size_t)NB * WR + WR);
 }
 // ------------------------------------------------------------------ host launchers
-template <typename T>
-struct BandPlan {
-    int nb = 16;
-    int grid = 0;
-    size_t smem = 0;
-};
 
 template <typename T, int NB>
 static cudaError_t launch_factor_nb(const BandArgs<T>& a, int grid, cudaStream_t st) {
@@ -241,26 +485,60 @@ static cudaError_t launch_factor_nb(const BandArgs<T>& a, int grid, cudaStream_t
     k_band_factor_solve<T, NB><<<grid, 256, smem, st>>>(a);
     return cudaGetLastError();
 }
-// Chooses the panel width that fits the shared-memory budget.
+
+// Panel width code: complex64 uses the blocked-panel kernel (code 64) when it fits, else the
+// generic kernel (negative codes); complex128 uses the generic kernel with the widest panel.
 template <typename T>
-int band_pick_nb(int b, size_t smem_optin) {
-    if (band_factor_smem<T, 32>(b) <= smem_optin) return 32;
-    if (band_factor_smem<T, 16>(b) <= smem_optin) return 16;
-    if (band_factor_smem<T, 8>(b) <= smem_optin) return 8;
+int band_pick_nb(int b, size_t smem_optin);
+template <>
+int band_pick_nb<double>(int b, size_t smem_optin) {
+    if (band_factor_smem<double, 32>(b) <= smem_optin) return 32;
+    if (band_factor_smem<double, 16>(b) <= smem_optin) return 16;
+    if (band_factor_smem<double, 8>(b) <= smem_optin) return 8;
+    return 0;
+}
+template <>
+int band_pick_nb<float>(int b, size_t smem_optin) {
+    if (band_factor_v4_smem(b) <= smem_optin) return 64;   // blocked panel of 32 (code 64)
+    if (band_factor_smem<float, 16>(b) <= smem_optin) return -16;  // generic kernel
+    if (band_factor_smem<float, 8>(b) <= smem_optin) return -8;
     return 0;
 }
 
 template <typename T>
-size_t band_smem_for(int nb, int b) {
-    return nb == 32 ? band_factor_smem<T, 32>(b) : nb == 16 ? band_factor_smem<T, 16>(b) : band_factor_smem<T, 8>(b);
+size_t band_smem_for(int nb, int b);
+template <>
+size_t band_smem_for<double>(int nb, int b) {
+    return nb == 32 ? band_factor_smem<double, 32>(b) : nb == 16 ? band_factor_smem<double, 16>(b)
+                                                                : band_factor_smem<double, 8>(b);
+}
+template <>
+size_t band_smem_for<float>(int nb, int b) {
+    if (nb == 64) return band_factor_v4_smem(b);
+    return nb == -16 ? band_factor_smem<float, 16>(b) : band_factor_smem<float, 8>(b);
 }
 
 template <typename T>
-cudaError_t band_factor_solve_launch(const BandArgs<T>& a, int nb, int grid, cudaStream_t st) {
-    if (nb == 32) return launch_factor_nb<T, 32>(a, grid, st);
-    if (nb == 16) return launch_factor_nb<T, 16>(a, grid, st);
-    return launch_factor_nb<T, 8>(a, grid, st);
+cudaError_t band_factor_solve_launch(const BandArgs<T>& a, int nb, int grid, cudaStream_t st);
+template <>
+cudaError_t band_factor_solve_launch<double>(const BandArgs<double>& a, int nb, int grid, cudaStream_t st) {
+    if (nb == 32) return launch_factor_nb<double, 32>(a, grid, st);
+    if (nb == 16) return launch_factor_nb<double, 16>(a, grid, st);
+    return launch_factor_nb<double, 8>(a, grid, st);
 }
+template <>
+cudaError_t band_factor_solve_launch<float>(const BandArgs<float>& a, int nb, int grid, cudaStream_t st) {
+    if (nb == 64) {
+        size_t smem = band_factor_v4_smem(a.b);
+        cudaError_t e = cudaFuncSetAttribute(k_band_factor_v4, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        k_band_factor_v4<<<grid, V4_THREADS, smem, st>>>(a);
+        return cudaGetLastError();
+    }
+    if (nb == -16) return launch_factor_nb<float, 16>(a, grid, st);
+    return launch_factor_nb<float, 8>(a, grid, st);
+}
+
 template <typename T, int NB>
 static int occupancy_nb(int b) {
     int occ = 0;
@@ -272,17 +550,23 @@ static int occupancy_nb(int b) {
 }
 
 template <typename T>
-int band_occupancy(int nb, int b) {
-    return nb == 32 ? occupancy_nb<T, 32>(b) : nb == 16 ? occupancy_nb<T, 16>(b) : occupancy_nb<T, 8>(b);
+int band_occupancy(int nb, int b);
+template <>
+int band_occupancy<double>(int nb, int b) {
+    return nb == 32 ? occupancy_nb<double, 32>(b) : nb == 16 ? occupancy_nb<double, 16>(b) : occupancy_nb<double, 8>(b);
+}
+template <>
+int band_occupancy<float>(int nb, int b) {
+    if (nb == 64) {
+        int occ = 0;
+        size_t smem = band_factor_v4_smem(b);
+        cudaFuncSetAttribute(k_band_factor_v4, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_band_factor_v4, V4_THREADS, smem);
+        cudaGetLastError();
+        return occ;
+    }
+    return nb == -16 ? occupancy_nb<float, 16>(b) : occupancy_nb<float, 8>(b);
 }
 
-template int band_occupancy<float>(int, int);
-template int band_occupancy<double>(int, int);
-template int band_pick_nb<float>(int, size_t);
-template int band_pick_nb<double>(int, size_t);
-template size_t band_smem_for<float>(int, int);
-template size_t band_smem_for<double>(int, int);
-template cudaError_t band_factor_solve_launch<float>(const BandArgs<float>&, int, int, cudaStream_t);
-template cudaError_t band_factor_solve_launch<double>(const BandArgs<double>&, int, int, cudaStream_t);
 
 }  // namespace stfdm
