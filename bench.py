@@ -53,6 +53,8 @@ def parse_args(argv=None):
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--profile-step", action="store_true",
                     help="set up, then run exactly one solve and exit (for ncu launch lists)")
+    ap.add_argument("--profile-xform", action="store_true",
+                    help="set up, then run one tensor-core forward time transform and exit (small device footprint)")
     return ap.parse_args(argv)
 
 
@@ -263,6 +265,12 @@ def run_ours(args):
     p0 = p0.to(dt)
     psi = torch.empty_like(F)
     info = {}
+    if args.profile_xform:
+        G32 = stfdm.st_time_transform(h, "Y", "mixed", F.to(torch.complex64))
+        torch.cuda.synchronize()
+        if rank == 0:
+            print(json.dumps({"profile_xform": args.config, "norm": float(torch.linalg.vector_norm(G32))}))
+        return 0
     if args.profile_step:
         _, info = stfdm.st_fdm_solve(h, F, p0, psi=psi, precision=args.precision)
         torch.cuda.synchronize()
@@ -293,9 +301,11 @@ def run_ours(args):
     t_ms = reduce_max(t_ms, world, dev)
     value = world * pr.unknowns / (t_ms * 1e-3)
     sweeps = int(info.get("sweeps", 1)) if info else 1
-    # our kernels per step: A_x psi0, (sweeps + 1) x (residual + reduction), sweeps x (2 transforms + band),
-    # final psi0 add   (mixed);  FP64/FP32: A_x psi0, 2 transforms, band
-    launches_per_step = (1 + 2 * (sweeps + 1) + 3 * sweeps + 1) if args.precision == "mixed" else 4
+    # our kernels per step (GMRES refinement, factors kept): A_x psi0, set_scalars, per restart cycle
+    # residual + reduction + scale, per FDM32 application 2 x (split + tensor-core GEMM), factor + backward
+    # (first) or forward + backward substitution, apply + reduction, 3 multi-dot pairs, 2 multi-axpy, scale;
+    # final combine and psi0 add.  The exact list of one step is in profiles/launches_mixed_c2.md.
+    launches_per_step = (2 + 3 * 2 + sweeps * (4 + 2 + 2 + 6 + 2 + 1) + 2 + 1) if args.precision == "mixed" else 6
 
     # ---- end to end through the C ABI with host buffers (H2D of F and psi0, D2H of psi)
     Fh = F.cpu().pin_memory()
@@ -361,7 +371,7 @@ def run_ours(args):
     lanes = 128 if kprec == "fp32" else 2             # FP32 / FP64 FMA lanes per SM per clock
     peak = props.multi_processor_count * lanes * 2 * max_mhz * 1e6 / 1e12
     achieved = flops / tk / 1e12
-    roof = {"bound": "alu", "kernel": f"k_band_factor_solve<{'float' if kprec == 'fp32' else 'double'},16>",
+    roof = {"bound": "alu", "kernel": "k_band_factor_v4 (complex64)" if kprec == "fp32" else "k_band_factor_solve<double,32>",
             "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
             "traffic": profiled_traffic(args.config), "launch_ms": tk * 1e3,
             "peak_basis": f"{props.multi_processor_count} SMs x {lanes} {kprec.upper()} FMA lanes x 2 x {max_mhz:.0f} MHz "

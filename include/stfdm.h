@@ -114,6 +114,7 @@ typedef struct {
     double kappa_x;              /* kappa_2(X_t) */
     double min_neg_im_shift;     /* min_k (-Im s_k); >= 0 up to rounding */
     double setup_seconds;        /* host time of st_fdm_setup's FP64 decomposition */
+    int tensor_cores;            /* 1 if the complex-FP32 time transforms ran on the tcgen05 tensor cores */
 } st_solve_info;
 
 /* ------------------------------------------------------------------ status */

@@ -49,7 +49,7 @@ class st_solve_opts(ctypes.Structure):
 class st_solve_info(ctypes.Structure):
     _fields_ = [("sweeps", c_int), ("factors_kept", c_int), ("rel_residual", c_double),
                 ("residual_history", c_double * 16), ("kappa_x", c_double), ("min_neg_im_shift", c_double),
-                ("setup_seconds", c_double)]
+                ("setup_seconds", c_double), ("tensor_cores", c_int)]
 
 
 # name -> (restype, argtypes); every entry point declared in include/stfdm.h

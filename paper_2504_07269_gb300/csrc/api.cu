@@ -122,6 +122,8 @@ void free_handle(st_fdm* h) {
     cudaFree(h->ws_kry);
     cudaFree(h->kry_ptrs);
     cudaFree(h->kry_small);
+    for (int i = 0; i < 4; ++i) cudaFree(h->tc_A[i]);
+    cudaFree(h->tc_bt);
     delete h;
 }
 
@@ -150,6 +152,49 @@ st_status xform(const TA* A2, int n_t, int n_x, const void* in, void* out, int c
     a.r1_v = r1_v;
     CUDA_TRY((xform_simt_launch<TA, TB, TC, TACC>(a, st)));
     return ST_OK;
+}
+
+// Complex-FP32 time transform: the tensor-core path (3xTF32, tcgen05 + TMA) when available,
+// else the SIMT kernel.  in: c128 (in_c128) or c64, scaled by *b_scale and conjugated if conj_b;
+// out: c128 (out_c128) or c64, with the epilogue options of the SIMT kernel.
+st_status ensure_tc_input(st_fdm* h) {
+    const size_t need = (size_t)2 * h->tc_N2_pad * h->tc_K_pad * sizeof(float);
+    if (h->tc_bt && h->tc_bt_bytes >= need) return ST_OK;
+    cudaFree(h->tc_bt);
+    h->tc_bt = nullptr;
+    h->tc_bt_bytes = 0;
+    st_status s = dev_alloc(reinterpret_cast<void**>(&h->tc_bt), need, "tensor-core input planes");
+    if (s != ST_OK) return s;
+    h->tc_bt_bytes = need;
+    CUDA_TRY(cudaMemset(h->tc_bt, 0, need));   // padding rows stay zero
+    if (!tc_make_map(&h->tc_mapB, h->tc_bt, 2 * h->tc_N2_pad, h->tc_K_pad))
+        return fail(ST_ERR_CUDA, "tensor map for the transform input");
+    return ST_OK;
+}
+
+st_status xform32(st_fdm* h, int which, const void* in, bool in_c128, const double* b_scale, int conj_b, void* out,
+                  bool out_c128, int conj_out, int accumulate, const double* out_scale, const void* add_row,
+                  const double2* r1_u, const double2* r1_v, cudaStream_t st) {
+    const int n_t = h->tm.n_t, n_x = h->sm.n_x;
+    if (h->tc_ok) {
+        st_status s = ensure_tc_input(h);
+        if (s != ST_OK) return s;
+        CUDA_TRY(tc_split_launch(in, in_c128, n_t, n_x, h->tc_K_pad, h->tc_N2_pad, b_scale, conj_b, h->tc_bt, st));
+        CUDA_TRY(tc_gemm_launch(h->tc_mapA[which], h->tc_mapB, h->tc_M_pad, h->tc_N2_pad, h->tc_K_pad, n_t, n_x, out,
+                                out_c128, conj_out, accumulate, out_scale, add_row, r1_u, r1_v, h->ws_status + 1, st));
+        return ST_OK;
+    }
+    const float* A = reinterpret_cast<float*>(h->xf32[which]);
+    if (in_c128 && !out_c128)
+        return xform<float, double, float, float>(A, n_t, n_x, in, out, conj_b, conj_out, accumulate, b_scale, out_scale,
+                                                  add_row, r1_u, r1_v, st);
+    if (!in_c128 && out_c128)
+        return xform<float, float, double, float>(A, n_t, n_x, in, out, conj_b, conj_out, accumulate, b_scale,
+                                                  out_scale, add_row, r1_u, r1_v, st);
+    if (!in_c128 && !out_c128)
+        return xform<float, float, float, float>(A, n_t, n_x, in, out, conj_b, conj_out, accumulate, b_scale, out_scale,
+                                                 add_row, r1_u, r1_v, st);
+    return fail(ST_ERR_UNSUPPORTED, "xform32: c128 -> c128");
 }
 
 // ------------------------------------------------------------------ banded solves
@@ -232,10 +277,11 @@ st_status band_run(st_fdm* h, C<T>* G, int mode, cudaStream_t st) {
 }
 
 st_status check_status_flag(st_fdm* h, cudaStream_t st) {
-    int flag = 0;
-    CUDA_TRY(cudaMemcpyAsync(&flag, h->ws_status, sizeof(int), cudaMemcpyDeviceToHost, st));
+    int flag[2] = {0, 0};
+    CUDA_TRY(cudaMemcpyAsync(flag, h->ws_status, 2 * sizeof(int), cudaMemcpyDeviceToHost, st));
     CUDA_TRY(cudaStreamSynchronize(st));
-    if (flag) return fail(ST_ERR_ZERO_PIVOT, "spatial solve: zero or non-finite pivot");
+    if (flag[1]) return fail(ST_ERR_TIMEOUT, "tensor-core transform: a bounded pipeline wait expired");
+    if (flag[0]) return fail(ST_ERR_ZERO_PIVOT, "spatial solve: zero or non-finite pivot");
     return ST_OK;
 }
 
@@ -282,13 +328,11 @@ st_status solve_fp32(st_fdm* h, const void* F, const void* psi0, void* psi, cuda
         CUDA_TRY(launch_stencil_A(h->sm, psi0, true, nullptr, 1.0, apsi0, st));
     }
     float2* G = reinterpret_cast<float2*>(h->ws_g32);
-    s = xform<float, float, float, float>(reinterpret_cast<float*>(h->xf32[XF_Y]), n_t, n_x, F, G, 0, 0, 0, nullptr,
-                                          nullptr, nullptr, psi0 ? h->Ym64 : nullptr, apsi0, st);
+    s = xform32(h, XF_Y, F, false, nullptr, 0, G, false, 0, 0, nullptr, nullptr, psi0 ? h->Ym64 : nullptr, apsi0, st);
     if (s != ST_OK) return s;
     s = band_run<float>(h, G, 0, st);
     if (s != ST_OK) return s;
-    return xform<float, float, float, float>(reinterpret_cast<float*>(h->xf32[XF_X]), n_t, n_x, G, psi, 0, 0, 0,
-                                             nullptr, nullptr, psi0, nullptr, nullptr, st);
+    return xform32(h, XF_X, G, false, nullptr, 0, psi, false, 0, 0, nullptr, psi0, nullptr, nullptr, st);
 }
 
 
@@ -321,7 +365,7 @@ st_status solve_mixed(st_fdm* h, bool adjoint, const void* F, const void* psi0, 
     const double* Bband = adjoint ? h->dt.BTb : h->dt.Bb;
     const double bsign = adjoint ? -1.0 : 1.0;
     CUDA_TRY(cudaMemsetAsync(psi, 0, (size_t)n_t * n_x * sizeof(double2), st));
-    CUDA_TRY(cudaMemsetAsync(h->ws_status, 0, sizeof(int), st));
+    CUDA_TRY(cudaMemsetAsync(h->ws_status, 0, 2 * sizeof(int), st));
     int sweeps = 0;
     double hist[16];
     int nh = 0;
@@ -347,13 +391,8 @@ st_status solve_mixed(st_fdm* h, bool adjoint, const void* F, const void* psi0, 
         }
         if (sw == nsweeps) break;
         // delta = K^{-1} R (or K^{-H} R) in complex FP32, psi += delta (scaled)
-        if (!adjoint) {
-            s = xform<float, double, float, float>(reinterpret_cast<float*>(h->xf32[XF_Y]), n_t, n_x, R, G, 0, 0, 0,
-                                                   scal + 2, nullptr, nullptr, nullptr, nullptr, st);
-        } else {
-            s = xform<float, double, float, float>(reinterpret_cast<float*>(h->xf32[XF_XT]), n_t, n_x, R, G, 1, 0, 0,
-                                                   scal + 2, nullptr, nullptr, nullptr, nullptr, st);
-        }
+        s = xform32(h, adjoint ? XF_XT : XF_Y, R, true, scal + 2, adjoint ? 1 : 0, G, false, 0, 0, nullptr, nullptr,
+                    nullptr, nullptr, st);
         if (s != ST_OK) return s;
         int mode = 0;
         if (keep) mode = (sw == 0) ? 1 : 2;
@@ -365,13 +404,8 @@ st_status solve_mixed(st_fdm* h, bool adjoint, const void* F, const void* psi0, 
             }
             if (s != ST_OK) return s;
         }
-        if (!adjoint) {
-            s = xform<float, float, double, float>(reinterpret_cast<float*>(h->xf32[XF_X]), n_t, n_x, G, psi, 0, 0, 1,
-                                                   nullptr, scal + 3, nullptr, nullptr, nullptr, st);
-        } else {
-            s = xform<float, float, double, float>(reinterpret_cast<float*>(h->xf32[XF_YT]), n_t, n_x, G, psi, 0, 1, 1,
-                                                   nullptr, scal + 3, nullptr, nullptr, nullptr, st);
-        }
+        s = xform32(h, adjoint ? XF_YT : XF_X, G, false, nullptr, 0, psi, true, adjoint ? 1 : 0, 1, scal + 3, nullptr,
+                    nullptr, nullptr, st);
         if (s != ST_OK) return s;
         ++sweeps;
     }
@@ -398,15 +432,9 @@ st_status solve_mixed(st_fdm* h, bool adjoint, const void* F, const void* psi0, 
 // Hessenberg least-squares problem (Givens rotations) is solved on the host.
 st_status precond32(st_fdm* h, bool adjoint, const double2* v, double2* z, bool& keep, bool& first,
                     const double* scal, cudaStream_t st) {
-    const int n_t = h->tm.n_t, n_x = h->sm.n_x;
     float2* G = reinterpret_cast<float2*>(h->ws_g32);
-    st_status s;
-    if (!adjoint)
-        s = xform<float, double, float, float>(reinterpret_cast<float*>(h->xf32[XF_Y]), n_t, n_x, v, G, 0, 0, 0,
-                                               scal, nullptr, nullptr, nullptr, nullptr, st);
-    else
-        s = xform<float, double, float, float>(reinterpret_cast<float*>(h->xf32[XF_XT]), n_t, n_x, v, G, 1, 0, 0,
-                                               scal, nullptr, nullptr, nullptr, nullptr, st);
+    st_status s = xform32(h, adjoint ? XF_XT : XF_Y, v, true, scal, adjoint ? 1 : 0, G, false, 0, 0, nullptr, nullptr,
+                          nullptr, nullptr, st);
     if (s != ST_OK) return s;
     int mode = keep ? (first ? 1 : 2) : 0;
     s = band_run<float>(h, G, mode, st);
@@ -416,11 +444,8 @@ st_status precond32(st_fdm* h, bool adjoint, const double2* v, double2* z, bool&
     }
     if (s != ST_OK) return s;
     first = false;
-    if (!adjoint)
-        return xform<float, float, double, float>(reinterpret_cast<float*>(h->xf32[XF_X]), n_t, n_x, G, z, 0, 0, 0,
-                                                  nullptr, scal + 1, nullptr, nullptr, nullptr, st);
-    return xform<float, float, double, float>(reinterpret_cast<float*>(h->xf32[XF_YT]), n_t, n_x, G, z, 0, 1, 0,
-                                              nullptr, scal + 1, nullptr, nullptr, nullptr, st);
+    return xform32(h, adjoint ? XF_YT : XF_X, G, false, nullptr, 0, z, true, adjoint ? 1 : 0, 0, scal + 1, nullptr,
+                   nullptr, nullptr, st);
 }
 
 st_status ensure_krylov(st_fdm* h, int m) {
@@ -495,7 +520,7 @@ st_status solve_mixed_gmres(st_fdm* h, bool adjoint, const void* F, const void* 
     const double psc = std::ldexp(1.0, (int)std::lround(0.5 * std::log2((double)N)));
     CUDA_TRY(launch_set_scalars(scal + 4, psc, 1.0 / psc, st));
     CUDA_TRY(cudaMemsetAsync(psi, 0, N * sizeof(double2), st));
-    CUDA_TRY(cudaMemsetAsync(h->ws_status, 0, sizeof(int), st));
+    CUDA_TRY(cudaMemsetAsync(h->ws_status, 0, 2 * sizeof(int), st));
     double2* x = reinterpret_cast<double2*>(psi);
     double hist[16];
     int nh = 0;
@@ -620,13 +645,11 @@ st_status adjoint_direct(st_fdm* h, bool fp32, const void* G, void* lambda, cuda
     s = grow(h->ws_g32, h->ws_g32_bytes, (size_t)n_t * n_x * sizeof(float2), "H32");
     if (s != ST_OK) return s;
     float2* H = reinterpret_cast<float2*>(h->ws_g32);
-    s = xform<float, float, float, float>(reinterpret_cast<float*>(h->xf32[XF_XT]), n_t, n_x, G, H, 1, 0, 0, nullptr,
-                                          nullptr, nullptr, nullptr, nullptr, st);
+    s = xform32(h, XF_XT, G, false, nullptr, 1, H, false, 0, 0, nullptr, nullptr, nullptr, nullptr, st);
     if (s != ST_OK) return s;
     s = band_run<float>(h, H, 0, st);
     if (s != ST_OK) return s;
-    return xform<float, float, float, float>(reinterpret_cast<float*>(h->xf32[XF_YT]), n_t, n_x, H, lambda, 0, 1, 0,
-                                             nullptr, nullptr, nullptr, nullptr, nullptr, st);
+    return xform32(h, XF_YT, H, false, nullptr, 0, lambda, false, 1, 0, nullptr, nullptr, nullptr, nullptr, st);
 }
 
 st_status validate_opts(const st_solve_opts* o, st_solve_opts& out) {
@@ -642,11 +665,12 @@ st_status validate_opts(const st_solve_opts* o, st_solve_opts& out) {
     return ST_OK;
 }
 
-void fill_info_common(const st_fdm* h, st_solve_info* info) {
+void fill_info_common(const st_fdm* h, st_solve_info* info, int precision) {
     if (!info) return;
     info->kappa_x = h->td.kappa;
     info->min_neg_im_shift = h->td.min_neg_im;
     info->setup_seconds = h->setup_seconds;
+    info->tensor_cores = (precision != ST_FP64 && h->tc_ok) ? 1 : 0;
 }
 
 }  // namespace
@@ -730,6 +754,20 @@ extern "C" st_status st_fdm_setup(const st_time* t, const st_space* sp, const st
         for (size_t i = 0; i < nn; ++i) f32[i] = make_float2((float)mats[w][i].real(), (float)mats[w][i].imag());
         s = upload(&h->xf32[w], f32.data(), nn * sizeof(float2), "transform (FP32)");
     }
+    // tensor-core transforms (sm_100 family): hi/lo TF32 splits of the four transform matrices
+    if (s == ST_OK && prop.major == 10) {
+        h->tc_M_pad = tc_round_up(n, 128);
+        h->tc_K_pad = tc_round_up(n, 32);
+        h->tc_N2_pad = tc_round_up(2 * h->sm.n_x, 128);
+        std::vector<float> sp((size_t)4 * h->tc_M_pad * h->tc_K_pad);
+        bool ok = true;
+        for (int w = 0; w < 4 && s == ST_OK && ok; ++w) {
+            tc_split_matrix(mats[w].data(), n, h->tc_M_pad, h->tc_K_pad, sp.data());
+            s = upload(&h->tc_A[w], sp.data(), sp.size() * sizeof(float), "tensor-core transform");
+            if (s == ST_OK) ok = tc_make_map(&h->tc_mapA[w], h->tc_A[w], 4 * h->tc_M_pad, h->tc_K_pad);
+        }
+        h->tc_ok = (s == ST_OK && ok) ? 1 : 0;
+    }
     std::vector<float2> s32(n);
     for (int k = 0; k < n; ++k) s32[k] = make_float2((float)h->td.s[k].real(), (float)h->td.s[k].imag());
     std::vector<cd> ym(n, 0.0);
@@ -789,12 +827,12 @@ extern "C" st_status st_fdm_solve(st_fdm* h, const void* F, const void* psi0, vo
     if (s != ST_OK) return s;
     DeviceGuard g(h->device);
     cudaStream_t st = S(stream);
-    fill_info_common(h, info);
+    fill_info_common(h, info, o.precision);
     if (o.precision == ST_MIXED) {
         if (o.fixed_sweeps > 0 || o.method == ST_REFINE_CLASSIC) return solve_mixed(h, false, F, psi0, psi, o, info, st);
         return solve_mixed_gmres(h, false, F, psi0, psi, o, info, st);
     }
-    CUDA_TRY(cudaMemsetAsync(h->ws_status, 0, sizeof(int), st));
+    CUDA_TRY(cudaMemsetAsync(h->ws_status, 0, 2 * sizeof(int), st));
     s = (o.precision == ST_FP64) ? solve_fp64(h, F, psi0, psi, st) : solve_fp32(h, F, psi0, psi, st);
     if (s != ST_OK) return s;
     if (info) {
@@ -842,12 +880,12 @@ extern "C" st_status st_adjoint_solve(st_fdm* h, const void* G, void* lambda, co
     if (s != ST_OK) return s;
     DeviceGuard g(h->device);
     cudaStream_t st = S(stream);
-    fill_info_common(h, info);
+    fill_info_common(h, info, o.precision);
     if (o.precision == ST_MIXED) {
         if (o.fixed_sweeps > 0 || o.method == ST_REFINE_CLASSIC) return solve_mixed(h, true, G, nullptr, lambda, o, info, st);
         return solve_mixed_gmres(h, true, G, nullptr, lambda, o, info, st);
     }
-    CUDA_TRY(cudaMemsetAsync(h->ws_status, 0, sizeof(int), st));
+    CUDA_TRY(cudaMemsetAsync(h->ws_status, 0, 2 * sizeof(int), st));
     s = adjoint_direct(h, o.precision == ST_FP32, G, lambda, st);
     if (s != ST_OK) return s;
     if (info) {
@@ -885,9 +923,15 @@ extern "C" st_status st_time_transform(st_fdm* h, int which, int precision, cons
     if (precision == ST_FP64)
         return xform<double, double, double, double>(reinterpret_cast<double*>(h->xf64[which]), n_t, n_x, in, out, 0,
                                                      0, 0, nullptr, nullptr, nullptr, nullptr, nullptr, st);
-    if (precision == ST_FP32 || precision == ST_MIXED)
+    if (precision == ST_FP32)
         return xform<float, float, float, float>(reinterpret_cast<float*>(h->xf32[which]), n_t, n_x, in, out, 0, 0, 0,
                                                  nullptr, nullptr, nullptr, nullptr, nullptr, st);
+    if (precision == ST_MIXED) {
+        CUDA_TRY(cudaMemsetAsync(h->ws_status, 0, 2 * sizeof(int), st));
+        st_status s = xform32(h, which, in, false, nullptr, 0, out, false, 0, 0, nullptr, nullptr, nullptr, nullptr, st);
+        if (s != ST_OK) return s;
+        return check_status_flag(h, st);
+    }
     return fail(ST_ERR_ARG, "st_time_transform: unknown precision");
 }
 
@@ -900,7 +944,7 @@ extern "C" st_status st_spatial_solve(st_fdm* h, int precision, const void* G, v
     if (precision != ST_FP64 && precision != ST_FP32 && precision != ST_MIXED)
         return fail(ST_ERR_ARG, "st_spatial_solve: unknown precision");
     if (W != G) CUDA_TRY(cudaMemcpyAsync(W, G, elems * esz, cudaMemcpyDeviceToDevice, st));
-    CUDA_TRY(cudaMemsetAsync(h->ws_status, 0, sizeof(int), st));
+    CUDA_TRY(cudaMemsetAsync(h->ws_status, 0, 2 * sizeof(int), st));
     st_status s = (precision == ST_FP64) ? band_run<double>(h, reinterpret_cast<double2*>(W), 0, st)
                                          : band_run<float>(h, reinterpret_cast<float2*>(W), 0, st);
     if (s != ST_OK) return s;

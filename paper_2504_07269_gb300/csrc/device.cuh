@@ -1,6 +1,7 @@
 // Device-side shared declarations: complex helpers, the solver handle, kernel launchers.
 #pragma once
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 #include <cstdint>
@@ -108,6 +109,16 @@ template <> cudaError_t band_factor_solve_launch<float>(const BandArgs<float>& a
 template <> cudaError_t band_factor_solve_launch<double>(const BandArgs<double>& a, int nb, int grid, cudaStream_t st);
 template <typename T> cudaError_t subst_launch(const BandArgs<T>& a, int k0, int nsys, bool fwd, cudaStream_t st);
 
+// tensor-core (tcgen05, 3xTF32) time transforms
+int tc_round_up(int v, int m);
+bool tc_make_map(CUtensorMap* map, const float* base, int rows, int cols);
+void tc_split_matrix(const cd* T, int n, int M_pad, int K_pad, float* out);
+cudaError_t tc_split_launch(const void* in, bool in_c128, int K, int N, int K_pad, int N2_pad, const double* scale,
+                            int conj, float* bt, cudaStream_t st);
+cudaError_t tc_gemm_launch(const CUtensorMap& mapA, const CUtensorMap& mapB, int M_pad, int N2_pad, int K_pad, int M,
+                           int N, void* out, bool out_c128, int conj_out, int accumulate, const double* out_scale,
+                           const void* add_row, const double2* r1_u, const double2* r1_v, int* err, cudaStream_t st);
+
 }  // namespace stfdm
 
 struct st_fdm {
@@ -148,6 +159,14 @@ struct st_fdm {
     void* kry_small = nullptr;    // multi-dot partials and coefficient buffers
     size_t kry_small_bytes = 0;
     int kry_m = 0;
+    // tensor-core transforms: split matrices [4 parts][M_pad][K_pad] per transform, input planes
+    int tc_ok = 0;
+    int tc_M_pad = 0, tc_K_pad = 0, tc_N2_pad = 0;
+    float* tc_A[4] = {nullptr, nullptr, nullptr, nullptr};
+    CUtensorMap tc_mapA[4];
+    float* tc_bt = nullptr;       // [2][N2_pad][K_pad]
+    size_t tc_bt_bytes = 0;
+    CUtensorMap tc_mapB;
     int factors_valid = 0;        // ws_L holds the factors of all n_t systems (keep mode)
     int factors_prec = -1;
 };

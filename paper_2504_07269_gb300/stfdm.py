@@ -110,7 +110,8 @@ def _opts(precision="fp64", tol=0.0, max_sweeps=0, keep_factors=-1, fixed_sweeps
 def _info_dict(info: _lib.st_solve_info):
     return dict(sweeps=info.sweeps, factors_kept=info.factors_kept, rel_residual=info.rel_residual,
                 residual_history=[v for v in info.residual_history if v >= 0], kappa_x=info.kappa_x,
-                min_neg_im_shift=info.min_neg_im_shift, setup_seconds=info.setup_seconds)
+                min_neg_im_shift=info.min_neg_im_shift, setup_seconds=info.setup_seconds,
+                tensor_cores=info.tensor_cores)
 
 
 # ------------------------------------------------------------------ assembly / setup
@@ -245,7 +246,8 @@ def st_fdm_solve_batched(hs, Fs, psi0s=None, psis=None, precision="fp64", tol=0.
 
 
 def st_time_transform(h: FdmHandle, which: str, precision: str, inp, out=None, stream=None):
-    dt = _dtype(precision)
+    """precision: "fp64" (c128), "fp32" (c64, SIMT) or "mixed" (c64 on the tensor cores, 3xTF32)."""
+    dt = torch.complex64 if precision in ("fp32", "mixed") else torch.complex128
     _check_st(h, inp, dt, "in")
     if out is None:
         out = torch.empty_like(inp)

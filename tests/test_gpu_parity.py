@@ -66,6 +66,7 @@ def test_c1_manufactured(dev):
     psi, info = stfdm.st_fdm_solve(h, Fd, p0, precision="mixed")
     assert rel(psi.cpu().numpy(), ref) <= 1e-9, info
     assert info["rel_residual"] <= 1e-12 and info["sweeps"] >= 1
+    assert info["tensor_cores"] == 1   # the FP32 transforms ran on tcgen05
     psi32, _ = stfdm.st_fdm_solve(h, Fd.to(torch.complex64), p0.to(torch.complex64), precision="fp32")
     e32 = rel(psi32.cpu().numpy(), ref)
     print(f"c1 fp32 rel. error {e32:.2e}")
@@ -140,7 +141,9 @@ def test_lifting_with_psi0(dev):
 @pytest.mark.parametrize("n,p,N", [(9, 1, 70), (12, 2, 33)])
 def test_time_transform_step(dev, n, p, N):
     """Steps 2 / 4 (and the adjoint transforms): out = T in, against the plain matrix product
-    with the library's own T (checked against the oracle's decomposition on the CPU)."""
+    with the library's own T (checked against the oracle's decomposition on the CPU); FP64 and
+    FP32 SIMT kernels and the tensor-core kernel (n_t not a multiple of the 128-row tile, ragged
+    column tiles)."""
     from paper_2504_07269_gb300 import stfdm
 
     t = synth.uniform_time_nodes(N, 1.0)
@@ -155,6 +158,10 @@ def test_time_transform_step(dev, n, p, N):
         assert rel(out.cpu().numpy(), ref) <= 1e-13, w
         out32 = stfdm.st_time_transform(h, w, "fp32", di.to(torch.complex64))
         assert rel(out32.cpu().numpy(), ref) <= 1e-5, w
+        # tensor cores (tcgen05, 3xTF32 split of both operands)
+        outtc = stfdm.st_time_transform(h, w, "mixed", di.to(torch.complex64))
+        etc = rel(outtc.cpu().numpy(), ref)
+        assert etc <= 1e-5, (w, etc)
 
 
 @pytest.mark.parametrize("n,p,N,Lx", [(17, 1, 6, 1.0), (40, 2, 3, 1.4)])
