@@ -301,11 +301,17 @@ def run_ours(args):
     t_ms = reduce_max(t_ms, world, dev)
     value = world * pr.unknowns / (t_ms * 1e-3)
     sweeps = int(info.get("sweeps", 1)) if info else 1
-    # our kernels per step (GMRES refinement, factors kept): A_x psi0, set_scalars, per restart cycle
-    # residual + reduction + scale, per FDM32 application 2 x (split + tensor-core GEMM), factor + backward
-    # (first) or forward + backward substitution, apply + reduction, 3 multi-dot pairs, 2 multi-axpy, scale;
-    # final combine and psi0 add.  The exact list of one step is in profiles/launches_mixed_c2.md.
-    launches_per_step = (2 + 3 * 2 + sweeps * (4 + 2 + 2 + 6 + 2 + 1) + 2 + 1) if args.precision == "mixed" else 6
+    # Our kernels per step (GMRES refinement, factors kept, tensor-core transforms), counted from the
+    # solver's control flow and matching the ncu launch list of one step:
+    #   A_x psi0 + set_scalars                                   2
+    #   per restart cycle: residual + reduction                  2
+    #   per non-final cycle: x += Z y                            1
+    #   per FDM32 application: 2 x (split + tcgen05 GEMM), factor (first) or forward substitution,
+    #     backward substitution, K z + reduction, 3 x (multi-dot + finalize), 2 multi-axpy, scale  17
+    #   psi0 added back                                          1
+    hist = [r for r in (info.get("residual_history") or []) if r >= 0] if info else []
+    cycles = max(1, len(hist))
+    launches_per_step = (17 * sweeps + 3 * cycles + 2) if args.precision == "mixed" else 6
 
     # ---- end to end through the C ABI with host buffers (H2D of F and psi0, D2H of psi)
     Fh = F.cpu().pin_memory()
