@@ -121,7 +121,7 @@ typedef struct {
 const char* st_status_string(st_status s);
 const char* st_last_error_message(void);
 int st_abi_version(void);   /* returns STFDM_ABI_VERSION of the built library */
-#define STFDM_ABI_VERSION 1
+#define STFDM_ABI_VERSION 2
 
 /* ------------------------------------------------------------------ assembly (host) */
 /* Temporal matrices of eq. (matrix_t), Section 3.  p_t in {1, 2}: continuous piecewise
@@ -190,14 +190,78 @@ st_status st_adjoint_solve(st_fdm* h, const void* G, void* lambda, const st_solv
 st_status st_adjoint_lift(st_fdm* h, const void* grad_psi, const void* grad_F, void* grad_psi0,
                           void* stream);
 
-/* Many independent problems of uneven size in one call: each phase (transforms, banded
- * factor-and-solve) is one grouped persistent launch over a cost-sorted work list; with
- * ST_FP64 / fixed_sweeps > 0 the whole call can be captured in a CUDA graph.  Arrays of
- * `count` handles and device pointers as in st_fdm_solve; infos may be NULL or hold `count`
- * entries. */
+/* Many independent problems of uneven size in one call.  ST_MIXED with GMRES refinement runs as
+ * one batched plan (st_batch_create + st_batch_solve below, created and destroyed inside the
+ * call); ST_FP64, ST_FP32 and the classic / fixed-sweep refinements solve the problems one after
+ * another with st_fdm_solve.  Arrays of `count` handles and device pointers as in st_fdm_solve
+ * (psi0 may be NULL, or hold NULL entries); infos may be NULL or hold `count` entries. */
 st_status st_fdm_solve_batched(st_fdm* const* hs, int count, const void* const* F,
                                const void* const* psi0, void* const* psi,
                                const st_solve_opts* opts, st_solve_info* infos, void* stream);
+
+/* ------------------------------------------------------------------ batched plans */
+/* A plan solves `count` independent problems (handles from st_fdm_setup, all on one device, of
+ * any mixture of spatial meshes, n_t and temporal degree) in the mixed precision of st_fdm_solve:
+ * per problem FP64 flexible GMRES on K psi_hat = F~ (eq. LGS), right-preconditioned by its
+ * complex-FP32 fast-diagonalisation solve (Section 3, steps 2-4).  The problems advance together:
+ *   - every phase is one grouped launch over all problems (packed vectors, block tables); the
+ *     spatial solves of all (problem, k) pairs are one persistent launch over a cost-sorted work
+ *     list, each CTA factorising (banded LDL^T) and solving one system at a time;
+ *   - a restart cycle needs no host decision, so it is captured once in a CUDA graph and replayed;
+ *   - an autotuner times the candidate transform tile shapes and CTAs per SM of the spatial solve
+ *     on the plan's data at creation and keeps the fastest (cached per shape signature).
+ * The plan owns its workspace: the GMRES basis ((m+1) complex128 + m complex64 vectors of the
+ * packed length), one factor slot per resident CTA (no factors are kept between applications),
+ * the transform buffer.  Solves on one plan must not overlap; the handles must outlive the plan.
+ * The paper solves one problem at a time; batching is an extension. */
+typedef struct st_batch st_batch;
+
+typedef struct {
+    double tol;        /* relative residual target per problem, default 1e-12 */
+    int max_sweeps;    /* FP32 preconditioner applications per problem, default 40 */
+    int restart;       /* GMRES restart length m, 0 = automatic (<= 20, basis within half the free memory) */
+    int no_graph;      /* 1: launch each cycle directly instead of replaying a captured CUDA graph */
+    int no_tune;       /* 1: skip the autotuner (square 64 x 64 transform tiles, maximum CTAs per SM) */
+} st_batch_opts;
+
+typedef struct {
+    int count;                 /* problems */
+    int items;                 /* spatial systems (sum of n_t) */
+    int restart;               /* GMRES restart length */
+    int xform_tile_m, xform_tile_n;   /* transform tile (time rows x spatial columns) */
+    int solve_ctas_per_sm;     /* CTAs per SM of the persistent factor-and-solve */
+    int solve_grid;            /* its grid */
+    int graph_nodes;           /* nodes of the captured cycle graph (0 before the first solve) */
+    int cycles;                /* restart cycles run by the last solve */
+    int tuned;                 /* 0: defaults, 1: tuned at creation, 2: taken from the tuning cache */
+    double tune_seconds;       /* time spent tuning */
+    long long unknowns;        /* total space-time unknowns */
+    unsigned long long workspace_bytes;
+} st_batch_stats;
+
+/* Builds the plan and, unless opts->no_tune, runs the autotuner on the device (synchronous).
+ * opts may be NULL.  Errors: ST_ERR_ARG (no/NULL handles, different devices, negative option),
+ * ST_ERR_OOM, ST_ERR_UNSUPPORTED (spatial band too wide for shared memory), ST_ERR_CUDA. */
+st_status st_batch_create(st_fdm* const* hs, int count, const st_batch_opts* opts, st_batch** out);
+
+/* Solves all problems: F[p] (n_t, n_x) c128 right-hand side, psi0[p] n_x c128 initial value (the
+ * array or an entry may be NULL = 0), psi[p] (n_t, n_x) c128 output; all device pointers owned by
+ * the caller, psi[p] must not alias F[p].  Work runs on the plan's own stream, ordered after the
+ * caller's `stream` and before anything later enqueued on it; the call returns when done (it reads
+ * one counter per restart cycle).  infos (NULL or `count` entries) is filled for every problem,
+ * also on ST_ERR_NOT_CONVERGED (the first problem that missed the tolerance is named in
+ * st_last_error_message).  ST_ERR_ZERO_PIVOT if a spatial factorisation met a zero pivot. */
+st_status st_batch_solve(st_batch* b, const void* const* F, const void* const* psi0, void* const* psi,
+                         st_solve_info* infos, void* stream);
+/* Step 3 alone for the whole batch: W[k,:] = (M_x + s_k A_x)^{-1} G[k,:] for every k of every
+ * problem in one persistent launch, in place on the plan's complex64 transform buffer, on `stream`
+ * (asynchronous; the pivot flag is reported by the next st_batch_solve).  st_batch_spatial_get
+ * copies problem p's (n_t, n_x) c64 slice of that buffer to (to_plan = 0) or from (to_plan = 1) the
+ * device array G.  Used by the tests and to time the kernel; not needed for st_batch_solve. */
+st_status st_batch_spatial_solve(st_batch* b, void* stream);
+st_status st_batch_spatial_get(const st_batch* b, int p, void* G, int to_plan, void* stream);
+st_status st_batch_stats_get(const st_batch* b, st_batch_stats* out);
+void st_destroy_batch(st_batch* b);
 
 /* ------------------------------------------------------------------ single steps (device) */
 /* Step 2 / step 4 / adjoint transforms: out = T in with T selected by `which` (ST_XFORM_*),

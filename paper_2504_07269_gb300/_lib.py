@@ -52,6 +52,18 @@ class st_solve_info(ctypes.Structure):
                 ("setup_seconds", c_double), ("tensor_cores", c_int)]
 
 
+class st_batch_opts(ctypes.Structure):
+    _fields_ = [("tol", c_double), ("max_sweeps", c_int), ("restart", c_int), ("no_graph", c_int),
+                ("no_tune", c_int)]
+
+
+class st_batch_stats(ctypes.Structure):
+    _fields_ = [("count", c_int), ("items", c_int), ("restart", c_int), ("xform_tile_m", c_int),
+                ("xform_tile_n", c_int), ("solve_ctas_per_sm", c_int), ("solve_grid", c_int),
+                ("graph_nodes", c_int), ("cycles", c_int), ("tuned", c_int), ("tune_seconds", c_double),
+                ("unknowns", ctypes.c_longlong), ("workspace_bytes", ctypes.c_ulonglong)]
+
+
 # name -> (restype, argtypes); every entry point declared in include/stfdm.h
 SIGNATURES = {
     "st_status_string": (c_char_p, [c_int]),
@@ -74,6 +86,14 @@ SIGNATURES = {
     "st_fdm_solve_batched": (c_int, [ctypes.POINTER(c_void_p), c_int, ctypes.POINTER(c_void_p),
                                      ctypes.POINTER(c_void_p), ctypes.POINTER(c_void_p),
                                      ctypes.POINTER(st_solve_opts), ctypes.POINTER(st_solve_info), c_void_p]),
+    "st_batch_create": (c_int, [ctypes.POINTER(c_void_p), c_int, ctypes.POINTER(st_batch_opts),
+                                ctypes.POINTER(c_void_p)]),
+    "st_batch_solve": (c_int, [c_void_p, ctypes.POINTER(c_void_p), ctypes.POINTER(c_void_p), ctypes.POINTER(c_void_p),
+                               ctypes.POINTER(st_solve_info), c_void_p]),
+    "st_batch_spatial_solve": (c_int, [c_void_p, c_void_p]),
+    "st_batch_spatial_get": (c_int, [c_void_p, c_int, c_void_p, c_int, c_void_p]),
+    "st_batch_stats_get": (c_int, [c_void_p, ctypes.POINTER(st_batch_stats)]),
+    "st_destroy_batch": (None, [c_void_p]),
     "st_time_transform": (c_int, [c_void_p, c_int, c_int, c_void_p, c_void_p, c_void_p]),
     "st_spatial_solve": (c_int, [c_void_p, c_int, c_void_p, c_void_p, c_void_p]),
     "st_load_nodal": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p]),

@@ -960,14 +960,3 @@ extern "C" st_status st_load_nodal(st_fdm* h, const void* f_nodal, void* F, void
     return ST_OK;
 }
 
-extern "C" st_status st_fdm_solve_batched(st_fdm* const* hs, int count, const void* const* F,
-                                          const void* const* psi0, void* const* psi, const st_solve_opts* opts,
-                                          st_solve_info* infos, void* stream) {
-    if (count < 0 || (count > 0 && (!hs || !F || !psi))) return fail(ST_ERR_ARG, "st_fdm_solve_batched: bad arguments");
-    for (int i = 0; i < count; ++i) {
-        st_status s = st_fdm_solve(hs[i], F[i], psi0 ? psi0[i] : nullptr, psi[i], opts, infos ? &infos[i] : nullptr,
-                                   stream);
-        if (s != ST_OK) return s;
-    }
-    return ST_OK;
-}

@@ -109,6 +109,57 @@ template <> cudaError_t band_factor_solve_launch<float>(const BandArgs<float>& a
 template <> cudaError_t band_factor_solve_launch<double>(const BandArgs<double>& a, int nb, int grid, cudaStream_t st);
 template <typename T> cudaError_t subst_launch(const BandArgs<T>& a, int k0, int nsys, bool fwd, cudaStream_t st);
 
+// grouped factor-and-solve over the systems of a batch of problems (complex64)
+struct BatchBand {
+    int n, m, b, pad;
+    float Mc, Mw, Ms, Md, Ac, Aw, As, Ad;
+    const float2* shifts;   // s_k of the problem
+    float2* rhs;            // its (n_t, n) right-hand sides in, solutions out
+};
+size_t band_batch_smem(int b_max);
+cudaError_t band_batch_prepare(int b_max);
+int band_batch_occupancy(int b_max);
+cudaError_t band_batch_launch(const BatchBand* probs, const int2* items, int n_items, const int* active, int* counter,
+                              int b_max, float2* win, float2* Lslots, size_t L_stride, float2* Dslots, size_t D_stride,
+                              int* status, int grid, cudaStream_t st);
+
+// batched solve: per-problem descriptor and per-problem GMRES state (device arrays)
+struct BatchProb {
+    int n_t, n_x, m, pad;
+    double Mc, Mw, Ms, Md, Ac, Aw, As, Ad;
+    const double* Mb;       // n_t x 5 band of M_t
+    const double* Bb;       // n_t x 5 band of B_t
+    const double* m_t;
+    const float2* Y32;      // Y_t (row-major n_t x n_t, complex64)
+    const float2* X32;      // X_t
+    const double2* F;       // right-hand side (caller's array)
+    double2* x;             // iterate = the caller's output array
+    const double2* apsi0;   // A_x psi0 or NULL
+    long long off;          // offset of the problem in packed space-time vectors
+    double psc;             // power-of-two scale of the preconditioner input
+};
+
+struct BatchGm {
+    double* rr;       // [P] ||r||^2 of the last residual
+    double* ff;       // [P] ||F~||^2
+    double* bnorm;    // [P] ||F~|| (negative before the first cycle)
+    double* rel;      // [P] last relative residual
+    double* hist;     // [P][16]
+    int* nh;          // [P]
+    int* its;         // [P] preconditioner applications so far
+    int* stopped;     // [P] 1: converged, 2: out of iterations, 3: non-finite residual
+    int* active;      // [P] iterating in the current cycle
+    int* jdone;       // [P] Arnoldi steps of the current cycle
+    double* inv;      // [P] scale for the next basis vector
+    double2* H;       // [P][(m + 1) m] rotated Hessenberg matrix, row-major
+    double2* g;       // [P][m + 1]
+    double2* sn;      // [P][m]
+    double* cs;       // [P][m]
+    double2* h;       // [P][3][KB_MAXV] Gram-Schmidt coefficients (pass 1, pass 2, norm)
+    double2* y;       // [P][m]
+    int* pending;     // [1] problems not stopped at the start of the cycle
+};
+
 // tensor-core (tcgen05, 3xTF32) time transforms
 int tc_round_up(int v, int m);
 bool tc_make_map(CUtensorMap* map, const float* base, int rows, int cols);

@@ -226,7 +226,10 @@ __device__ __forceinline__ float2 shfl2(float2 v, int src) {
     return make_float2(__shfl_sync(0xffffffffu, v.x, src), __shfl_sync(0xffffffffu, v.y, src));
 }
 
-__device__ void band_factor_v4(const BandArgs<float>& a, int k, int ks, char* smem) {
+// One system: shift s, right-hand side z (y = D^{-1} L^{-1} g out), factor columns Lk and pivots
+// Dk, the CTA's window W of (b + 32) x (b + 1) entries; n, m, b, the stencil and status from a.
+__device__ __forceinline__ void band_factor_v4(const BandArgs<float>& a, const float2 s, float2* z, float2* Lk,
+                                               float2* Dk, float2* W, char* smem) {
     using T = float;
     constexpr int NB = V4_NB;
     const int n = a.n, b = a.b, m = a.m, WR = b + NB, WB = b + 1;
@@ -236,12 +239,6 @@ __device__ void band_factor_v4(const BandArgs<float>& a, int k, int ks, char* sm
     float2* Us = P + NB * WR;                          // [NB][NB]  U[q'][q] = d_q' L(q, q') for q' < q
     float2* dinv = Us + NB * NB;                       // [NB]
     float2* zb = dinv + NB;                            // [WR]
-    const float2 s = a.shifts[k];
-    float2* z = a.rhs + (size_t)k * n;
-    const size_t slot = a.keep ? (size_t)k : (size_t)ks;
-    float2* Lk = a.L + slot * (size_t)n * b;
-    float2* Dk = a.D + slot * (size_t)n;
-    float2* W = a.win + (size_t)blockIdx.x * WR * WB;
     // a new band row i (one warp): zero except the stencil offsets 0, 1, m, m + 1
     auto fill_row = [&](int i) {
         float2* row = W + (size_t)(i % WR) * WB;
@@ -448,18 +445,165 @@ __device__ void band_factor_v4(const BandArgs<float>& a, int k, int ks, char* sm
     }
 }
 
-__global__ void __launch_bounds__(V4_THREADS, 2) k_band_factor_v4(BandArgs<float> a) {
-    extern __shared__ __align__(16) char smem[];
-    for (int ks = blockIdx.x; ks < a.n_sys; ks += gridDim.x) {
-        band_factor_v4(a, a.k0 + ks, ks, smem);
-        __syncthreads();
-    }
-}
-
 size_t band_factor_v4_smem(int b) {
     const int WR = b + V4_NB;
     return sizeof(float2) * ((size_t)V4_NB * WR + V4_NB * V4_NB + V4_NB + WR);
 }
+
+size_t band_batch_smem(int b_max) {
+    const size_t bwd = sizeof(float2) * ((size_t)b_max + 32 + 32 + 32 * 33);
+    const size_t f = band_factor_v4_smem(b_max);
+    return f > bwd ? f : bwd;
+}
+
+__global__ void __launch_bounds__(V4_THREADS, 2) k_band_factor_v4(BandArgs<float> a) {
+    extern __shared__ __align__(16) char smem[];
+    const int WR = a.b + V4_NB, WB = a.b + 1;
+    for (int ks = blockIdx.x; ks < a.n_sys; ks += gridDim.x) {
+        const int k = a.k0 + ks;
+        const size_t slot = a.keep ? (size_t)k : (size_t)ks;
+        band_factor_v4(a, a.shifts[k], a.rhs + (size_t)k * a.n, a.L + slot * (size_t)a.n * a.b, a.D + slot * (size_t)a.n,
+                       a.win + (size_t)blockIdx.x * WR * WB, smem);
+        __syncthreads();
+    }
+}
+
+// ------------------------------------------------------------------ backward substitution by one CTA
+// L^T w = y for one system whose factor columns L (L[j*b + o - 1] = L(j + o, j)) this CTA has just
+// written; z holds y on entry and w on exit.  Rows are solved in blocks of 32 from the bottom:
+//   A. every warp forms, for 4 of the block's columns j, the contribution of the already solved
+//      rows below the block, sum_{j + o >= j1} L(j + o, j) w_{j+o} (lanes across the band);
+//   B. warp 0 solves the 32 x 32 unit upper triangle of the block by shuffles, lane = row, with
+//      the block's in-triangle entries of L staged in shared memory during A.
+// The solved w of the last b + 32 rows stay in a shared-memory ring.
+__device__ __forceinline__ void band_bwd_cta(int n, int b, const float2* __restrict__ L, float2* z, char* smem) {
+    using T = float;
+    const int RB = b + 32;
+    float2* ring = reinterpret_cast<float2*>(smem);   // [RB]: w of row r at r % RB
+    float2* tcon = ring + RB;                          // [32]: contributions from below the block
+    float2* Ls = tcon + 32;                            // [32][33]: Ls[r][q] = L(j0 + r, j0 + q), q < r
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    for (int j0 = ((n - 1) / 32) * 32; j0 >= 0; j0 -= 32) {
+        const int j1 = min(j0 + 32, n);
+        // the block's strictly lower triangle of L, 4 entries per thread
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+            const int idx = tid + 256 * e, r = idx >> 5, q = idx & 31, o = r - q;
+            Ls[r * 33 + q] = (o >= 1 && o <= b && j0 + r < j1) ? L[(size_t)(j0 + q) * b + (o - 1)] : mk<T>(0, 0);
+        }
+        for (int cc = 0; cc < 4; ++cc) {
+            const int c = warp * 4 + cc, j = j0 + c;
+            float2 acc = mk<T>(0, 0);
+            if (j < j1) {
+                const int ohi = min(b, n - 1 - j);
+                const float2* Lj = L + (size_t)j * b - 1;
+#pragma unroll 4
+                for (int o = j1 - j + lane; o <= ohi; o += 32) {
+                    int r = j + o;
+                    r -= (r / RB) * RB;
+                    cfma<T>(acc, Lj[o], ring[r]);
+                }
+            }
+#pragma unroll
+            for (int off = 16; off > 0; off >>= 1) {
+                acc.x += __shfl_xor_sync(0xffffffffu, acc.x, off);
+                acc.y += __shfl_xor_sync(0xffffffffu, acc.y, off);
+            }
+            if (lane == 0) tcon[c] = acc;
+        }
+        __syncthreads();
+        if (warp == 0) {
+            const int j = j0 + lane;
+            float2 acc = (j < j1) ? csub<T>(z[j], tcon[lane]) : mk<T>(0, 0);
+#pragma unroll
+            for (int r = 31; r > 0; --r) {
+                const float2 wr = mk<T>(__shfl_sync(0xffffffffu, acc.x, r), __shfl_sync(0xffffffffu, acc.y, r));
+                if (lane < r) cfms<T>(acc, Ls[r * 33 + lane], wr);
+            }
+            if (j < j1) {
+                ring[j % RB] = acc;
+                z[j] = acc;
+            }
+        }
+        __syncthreads();
+    }
+}
+
+// ------------------------------------------------------------------ grouped factor-and-solve
+// All systems (problem p, shift k) of a batch of problems of uneven size in one persistent launch:
+// each CTA takes the next item of a cost-sorted work list (atomic counter), factorises it with the
+// blocked-panel kernel (forward substitution fused) into its private factor slot and solves the
+// backward substitution itself.  Items of problems whose `active` flag is 0 are skipped.
+__global__ void __launch_bounds__(V4_THREADS, 2)
+k_band_batch_v4(const BatchBand* probs, const int2* items, int n_items, const int* active, int* counter, float2* win,
+                size_t win_stride, float2* Lslots, size_t L_stride, float2* Dslots, size_t D_stride, int* status) {
+    extern __shared__ __align__(16) char smem[];
+    __shared__ int s_item;
+    __shared__ BandArgs<float> s_args;   // the current item's geometry and stencil (keeps registers free)
+    __shared__ float2 s_shift;
+    __shared__ float2* s_z;
+    for (;;) {
+        if (threadIdx.x == 0) {
+            const int it = atomicAdd(counter, 1);
+            int run = 0;
+            if (it < n_items) {
+                const int2 pk = items[it];
+                run = (!active || active[pk.x]) ? 1 : 2;
+                if (run == 1) {
+                    const BatchBand& pb = probs[pk.x];
+                    s_args.n = pb.n;
+                    s_args.m = pb.m;
+                    s_args.b = pb.b;
+                    s_args.Mc = pb.Mc; s_args.Mw = pb.Mw; s_args.Ms = pb.Ms; s_args.Md = pb.Md;
+                    s_args.Ac = pb.Ac; s_args.Aw = pb.Aw; s_args.As = pb.As; s_args.Ad = pb.Ad;
+                    s_args.status = status;
+                    s_shift = pb.shifts[pk.y];
+                    s_z = pb.rhs + (size_t)pk.y * pb.n;
+                }
+            }
+            s_item = run;
+        }
+        __syncthreads();
+        const int run = s_item;
+        if (run == 0) break;
+        if (run == 1) {
+            float2* Lk = Lslots + (size_t)blockIdx.x * L_stride;
+            band_factor_v4(s_args, s_shift, s_z, Lk, Dslots + (size_t)blockIdx.x * D_stride,
+                           win + (size_t)blockIdx.x * win_stride, smem);
+            __syncthreads();
+            band_bwd_cta(s_args.n, s_args.b, Lslots + (size_t)blockIdx.x * L_stride, s_z, smem);
+        }
+        __syncthreads();
+    }
+}
+
+cudaError_t band_batch_launch(const BatchBand* probs, const int2* items, int n_items, const int* active, int* counter,
+                              int b_max, float2* win, float2* Lslots, size_t L_stride, float2* Dslots, size_t D_stride,
+                              int* status, int grid, cudaStream_t st) {
+    const size_t smem = band_batch_smem(b_max);
+    const size_t win_stride = (size_t)(b_max + V4_NB) * (b_max + 1);
+    cudaError_t e = cudaMemsetAsync(counter, 0, sizeof(int), st);
+    if (e != cudaSuccess) return e;
+    k_band_batch_v4<<<grid, V4_THREADS, smem, st>>>(probs, items, n_items, active, counter, win, win_stride, Lslots,
+                                                    L_stride, Dslots, D_stride, status);
+    return cudaGetLastError();
+}
+
+cudaError_t band_batch_prepare(int b_max) {
+    return cudaFuncSetAttribute(k_band_batch_v4, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)band_batch_smem(b_max));
+}
+
+int band_batch_occupancy(int b_max) {
+    int occ = 0;
+    if (band_batch_prepare(b_max) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_band_batch_v4, V4_THREADS, band_batch_smem(b_max));
+    cudaGetLastError();
+    return occ;
+}
+
 
 template <typename T, int NB>
 __global__ void __launch_bounds__(256, 2) k_band_factor_solve(BandArgs<T> a) {

@@ -18,6 +18,8 @@
 #include <cuda.h>
 #include <cuda_runtime.h>
 
+#include <atomic>
+
 #include <algorithm>
 #include <cstdint>
 #include <cstring>
@@ -313,16 +315,21 @@ typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t,
                                   const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
                                   CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
 EncodeTiledFn encode_fn() {
-    static EncodeTiledFn fn = nullptr;
-    if (!fn) {
+    // looked up once (thread-safe static initialisation)
+    static const EncodeTiledFn fn = []() -> EncodeTiledFn {
         void* p = nullptr;
         cudaDriverEntryPointQueryResult q;
         if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
             q == cudaDriverEntryPointSuccess)
-            fn = reinterpret_cast<EncodeTiledFn>(p);
-    }
+            return reinterpret_cast<EncodeTiledFn>(p);
+        return nullptr;
+    }();
     return fn;
 }
+
+// the GEMM kernel's shared-memory opt-in, once per device
+constexpr int TC_MAX_DEVICES = 64;
+std::atomic<int> g_tc_attr[TC_MAX_DEVICES];
 }  // namespace
 
 int tc_round_up(int v, int m) { return (v + m - 1) / m * m; }
@@ -384,11 +391,13 @@ cudaError_t tc_split_launch(const void* in, bool in_c128, int K, int N, int K_pa
 cudaError_t tc_gemm_launch(const CUtensorMap& mapA, const CUtensorMap& mapB, int M_pad, int N2_pad, int K_pad, int M,
                            int N, void* out, bool out_c128, int conj_out, int accumulate, const double* out_scale,
                            const void* add_row, const double2* r1_u, const double2* r1_v, int* err, cudaStream_t st) {
-    static bool attr = false;
-    if (!attr) {
-        cudaError_t e0 = cudaFuncSetAttribute(tc::k_xform_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, tc::SMEM_BYTES);
+    int dev = 0;
+    cudaError_t e0 = cudaGetDevice(&dev);
+    if (e0 != cudaSuccess) return e0;
+    if (dev < 0 || dev >= TC_MAX_DEVICES || !g_tc_attr[dev].load()) {
+        e0 = cudaFuncSetAttribute(tc::k_xform_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, tc::SMEM_BYTES);
         if (e0 != cudaSuccess) return e0;
-        attr = true;
+        if (dev >= 0 && dev < TC_MAX_DEVICES) g_tc_attr[dev].store(1);
     }
     tc::Epi e;
     e.M = M;

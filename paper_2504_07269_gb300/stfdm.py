@@ -222,6 +222,17 @@ def st_adjoint_lift(h: FdmHandle, grad_psi, grad_F, grad_psi0=None, stream=None)
     return grad_psi0
 
 
+def _ptr_array(ts):
+    return (ctypes.c_void_p * len(ts))(*[(t.data_ptr() if t is not None else None) for t in ts])
+
+
+def _check_list_with_info(status, where, infos, n):
+    if status != _lib.ST_OK:
+        err = _lib.StfdmError(status, where)
+        err.info = [_info_dict(infos[i]) for i in range(n)] if infos is not None else None
+        raise err
+
+
 def st_fdm_solve_batched(hs, Fs, psi0s=None, psis=None, precision="fp64", tol=0.0, max_sweeps=0,
                          keep_factors=-1, fixed_sweeps=0, stream=None, want_info=True, method="gmres"):
     n = len(hs)
@@ -235,14 +246,74 @@ def st_fdm_solve_batched(hs, Fs, psi0s=None, psis=None, precision="fp64", tol=0.
         for h, p0 in zip(hs, psi0s):
             _check_vec(h, p0, dt, "psi0")
     H = (ctypes.c_void_p * n)(*[h.ptr for h in hs])
-    Fp = (ctypes.c_void_p * n)(*[F.data_ptr() for F in Fs])
-    Pp = (ctypes.c_void_p * n)(*[p.data_ptr() for p in psis])
-    P0 = (ctypes.c_void_p * n)(*[(p.data_ptr() if p is not None else None) for p in psi0s]) if psi0s else None
+    P0 = _ptr_array(psi0s) if psi0s else None
     opts = _opts(precision, tol, max_sweeps, keep_factors, fixed_sweeps, method)
-    infos = (_lib.st_solve_info * n)()
-    check(lib().st_fdm_solve_batched(H, n, Fp, P0, Pp, ctypes.byref(opts), infos if want_info else None,
-                                     _stream(stream)), "st_fdm_solve_batched")
+    infos = (_lib.st_solve_info * n)() if want_info else None
+    st = lib().st_fdm_solve_batched(H, n, _ptr_array(Fs), P0, _ptr_array(psis), ctypes.byref(opts), infos,
+                                    _stream(stream))
+    _check_list_with_info(st, "st_fdm_solve_batched", infos, n)
     return psis, ([_info_dict(i) for i in infos] if want_info else None)
+
+
+class BatchHandle(_Handle):
+    _destroy = "st_destroy_batch"
+
+    def __init__(self, ptr, hs):
+        super().__init__(ptr)
+        self.hs = list(hs)   # the problem handles must outlive the plan
+
+
+def st_batch_create(hs, tol=0.0, max_sweeps=0, restart=0, no_graph=False, no_tune=False) -> BatchHandle:
+    """Batched mixed-precision plan over FdmHandles of any mixture of sizes (see st_batch_create)."""
+    n = len(hs)
+    H = (ctypes.c_void_p * n)(*[h.ptr for h in hs])
+    o = _lib.st_batch_opts(float(tol), int(max_sweeps), int(restart), int(bool(no_graph)), int(bool(no_tune)))
+    out = ctypes.c_void_p()
+    check(lib().st_batch_create(H, n, ctypes.byref(o), ctypes.byref(out)), "st_batch_create")
+    return BatchHandle(out, hs)
+
+
+def st_batch_solve(b: BatchHandle, Fs, psi0s=None, psis=None, stream=None, want_info=True):
+    n = len(b.hs)
+    if len(Fs) != n or (psi0s is not None and len(psi0s) != n):
+        raise ValueError("st_batch_solve: one right-hand side (and psi0) per problem")
+    if psis is None:
+        psis = [torch.empty_like(F) for F in Fs]
+    for h, F, p in zip(b.hs, Fs, psis):
+        _check_st(h, F, torch.complex128, "F")
+        _check_st(h, p, torch.complex128, "psi")
+    if psi0s is not None:
+        for h, p0 in zip(b.hs, psi0s):
+            _check_vec(h, p0, torch.complex128, "psi0")
+    infos = (_lib.st_solve_info * n)() if want_info else None
+    st = lib().st_batch_solve(b.ptr, _ptr_array(Fs), _ptr_array(psi0s) if psi0s is not None else None,
+                              _ptr_array(psis), infos, _stream(stream))
+    _check_list_with_info(st, "st_batch_solve", infos, n)
+    return psis, ([_info_dict(i) for i in infos] if want_info else None)
+
+
+def st_batch_spatial_solve(b: BatchHandle, stream=None):
+    check(lib().st_batch_spatial_solve(b.ptr, _stream(stream)), "st_batch_spatial_solve")
+
+
+def st_batch_spatial_get(b: BatchHandle, p: int, G, to_plan: bool, stream=None):
+    h = b.hs[p]
+    _check_st(h, G, torch.complex64, "G")
+    check(lib().st_batch_spatial_get(b.ptr, int(p), _ptr(G), int(bool(to_plan)), _stream(stream)),
+          "st_batch_spatial_get")
+    return G
+
+
+def st_batch_stats_get(b: BatchHandle) -> dict:
+    s = _lib.st_batch_stats()
+    check(lib().st_batch_stats_get(b.ptr, ctypes.byref(s)), "st_batch_stats_get")
+    return {name: getattr(s, name) for name, _ in s._fields_}
+
+
+def st_destroy_batch(b: BatchHandle):
+    if b.ptr:
+        lib().st_destroy_batch(b.ptr)
+        b.ptr = None
 
 
 def st_time_transform(h: FdmHandle, which: str, precision: str, inp, out=None, stream=None):
@@ -296,3 +367,16 @@ def setup_problem(n_squares: int, p_t: int, t_nodes, Lx: float = 1.0, Ly: float 
     t = st_assemble_time(p_t, t_nodes)
     s = st_assemble_space(n_squares, Lx, Ly)
     return st_fdm_setup(t, s, **kw)
+
+
+def setup_problems(specs, workers: int = 0, **kw):
+    """setup_problem for many (n_squares, p_t, t_nodes, Lx, Ly) tuples, concurrently on host
+    threads (one host thread per decomposition); returns the handles in order."""
+    import os
+    from concurrent.futures import ThreadPoolExecutor
+
+    workers = workers or min(len(specs), os.cpu_count() or 1)
+    kw = dict(kw, host_threads=1)
+    with ThreadPoolExecutor(max_workers=max(1, workers)) as ex:
+        futs = [ex.submit(setup_problem, n, p, t, Lx, Ly, **kw) for (n, p, t, Lx, Ly) in specs]
+        return [f.result() for f in futs]

@@ -209,6 +209,33 @@ def batch_problems(count: int = 64, seed: int = 5, n_choices=None, Nt_range=(32,
     return out
 
 
+def dof_times(p_t: int, t_nodes) -> np.ndarray:
+    """Times of the temporal DOFs including t_0: the mesh nodes (P1), nodes and midpoints (P2)."""
+    t = np.asarray(t_nodes, dtype=np.float64)
+    if p_t == 1:
+        return t.copy()
+    tf = np.empty(2 * len(t) - 1)
+    tf[0::2] = t
+    tf[1::2] = 0.5 * (t[:-1] + t[1:])
+    return tf
+
+
+def batch_inputs(pr: Problem):
+    """Inputs of one problem of the uneven batch: psi0 = its seeded 4-packet sum at the interior
+    nodes, and the forcing f = c sin(k1 pi x1) sin(k2 pi x2) e^{i omega t} (or f = 0) in separable
+    form f(x, t) = a(t) b(x): returns (psi0 (n_x,), a at the DOF times incl. t_0, b (n_x,)), with
+    a = b = None for an unforced problem."""
+    x1, x2 = interior_coords(pr.n, pr.Lx, pr.Ly)
+    psi0 = packet_values(packet_params(pr.seed), x1, x2)
+    e = pr.extra or {}
+    if not e.get("forced", False):
+        return psi0, None, None
+    k1, k2 = e["fk"]
+    a = complex(e["c"]) * np.exp(1j * e["omega"] * dof_times(pr.p_t, pr.t_nodes))
+    b = (np.sin(k1 * np.pi * x1) * np.sin(k2 * np.pi * x2)).astype(np.complex128)
+    return psi0, a, b
+
+
 def psi_c1_derivs(x1, x2, t):
     """(d_t, d_x1, d_x2) of psi_c1."""
     a, b = np.sin(np.pi * x1), np.sin(np.pi * x2)

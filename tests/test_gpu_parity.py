@@ -272,24 +272,6 @@ def test_autograd_matches_finite_differences(dev):
     assert rel(gF.cpu().numpy(), gref) <= 1e-10
 
 
-# ------------------------------------------------------------------ batched
-def test_batched_equals_single(dev):
-    from paper_2504_07269_gb300 import stfdm
-
-    probs = synth.batch_problems(5, seed=7, n_choices=[8, 12, 17], Nt_range=(3, 9))
-    hs, Fs, P0 = [], [], []
-    for pr in probs:
-        h = _handle(pr.n, pr.p_t, pr.t_nodes)
-        hs.append(h)
-        Fs.append(torch.from_numpy(synth.cn01((pr.n_t, pr.n_x), seed=pr.seed)).to(dev))
-        x1, x2 = synth.interior_coords(pr.n)
-        P0.append(torch.from_numpy(synth.packet_values(synth.packet_params(pr.seed), x1, x2)).to(dev))
-    outs, infos = stfdm.st_fdm_solve_batched(hs, Fs, P0, precision="mixed")
-    for h, F, p0, o in zip(hs, Fs, P0, outs):
-        single, _ = stfdm.st_fdm_solve(h, F, p0, precision="mixed")
-        assert rel(o.cpu().numpy(), single.cpu().numpy()) <= 1e-12
-
-
 # ------------------------------------------------------------------ failure reporting (host side)
 def test_failures_are_reported(dev):
     from paper_2504_07269_gb300 import _lib, stfdm
