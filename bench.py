@@ -341,6 +341,7 @@ def run_ours(args):
     # ---- error against the FP64 FDM on the same inputs
     err = None
     fp64_value = None
+    fp32_value = fp32_err = None
     if not args.no_fp64_check and args.precision != "fp64":
         ref = torch.empty(F.shape, dtype=torch.complex128, device=dev)
         F64, p064 = F.to(torch.complex128), p0.to(torch.complex128)
@@ -353,7 +354,18 @@ def run_ours(args):
         fp64_value = pr.unknowns / (e0.elapsed_time(e1) * 1e-3)
         stfdm.st_fdm_solve(h, F, p0, psi=psi, precision=args.precision, want_info=False)
         err = float(torch.linalg.vector_norm(psi.to(torch.complex128) - ref) / torch.linalg.vector_norm(ref))
-        del ref, F64, p064
+        # the plain complex-FP32 FDM on the same inputs (3xTF32 tensor-core transforms, FP32 solves)
+        F32, p032 = F.to(torch.complex64), p0.to(torch.complex64)
+        psi32 = torch.empty_like(F32)
+        stfdm.st_fdm_solve(h, F32, p032, psi=psi32, precision="fp32", want_info=False)
+        torch.cuda.synchronize()
+        e0.record()
+        stfdm.st_fdm_solve(h, F32, p032, psi=psi32, precision="fp32", want_info=False)
+        e1.record()
+        torch.cuda.synchronize()
+        fp32_value = pr.unknowns / (e0.elapsed_time(e1) * 1e-3)
+        fp32_err = float(torch.linalg.vector_norm(psi32.to(torch.complex128) - ref) / torch.linalg.vector_norm(ref))
+        del ref, F64, p064, F32, p032, psi32
 
     # ---- roofline of the dominant kernel: the banded LDL^T factor-and-solve (FP32 / FP64)
     kprec = "fp64" if args.precision == "fp64" else "fp32"
@@ -394,7 +406,8 @@ def run_ours(args):
                 "warmup": args.warmup, "ms_per_step": t_ms, "higher_is_better": True, "scaling": "weak",
                 "vs_baseline": None, "dtype": {"mixed": "c64+f64", "fp64": "f64", "fp32": "f32"}[args.precision],
                 "data": "synthetic (manufactured solution, interpolated load)", "config": _config(pr, args),
-                "err_vs_fp64": err, "fp64_fdm_unknowns_per_s": fp64_value, "sweeps": sweeps,
+                "err_vs_fp64": err, "fp64_fdm_unknowns_per_s": fp64_value,
+                "fp32_fdm_unknowns_per_s": fp32_value, "fp32_fdm_err_vs_fp64": fp32_err, "sweeps": sweeps,
                 "final_rel_residual": info.get("rel_residual") if info else None,
                 "setup_s": setup_s, "kappa_x": h.kappa,
                 "e2e": {"value": world * pr.unknowns / (e2e_ms * 1e-3), "unit": UNIT, "h2d_bytes_per_step": h2d,
