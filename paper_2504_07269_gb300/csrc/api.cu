@@ -280,7 +280,7 @@ st_status check_status_flag(st_fdm* h, cudaStream_t st) {
     int flag[2] = {0, 0};
     CUDA_TRY(cudaMemcpyAsync(flag, h->ws_status, 2 * sizeof(int), cudaMemcpyDeviceToHost, st));
     CUDA_TRY(cudaStreamSynchronize(st));
-    if (flag[1]) return fail(ST_ERR_TIMEOUT, "tensor-core transform: a bounded pipeline wait expired");
+    if (flag[1]) return fail(ST_ERR_TIMEOUT, "a bounded pipeline wait expired (tensor-core transform or factor streaming)");
     if (flag[0]) return fail(ST_ERR_ZERO_PIVOT, "spatial solve: zero or non-finite pivot");
     return ST_OK;
 }
