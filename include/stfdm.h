@@ -279,6 +279,26 @@ st_status st_spatial_solve(st_fdm* h, int precision, const void* G, void* W, voi
  * F (n_t, n_x) c128 (device).  Assembly helper, not part of the solve. */
 st_status st_load_nodal(st_fdm* h, const void* f_nodal, void* F, void* stream);
 
+/* ------------------------------------------------------------------ manufactured solutions */
+/* Exact solutions for error measurement (Section 4): */
+#define ST_EXACT_C1 0     /* psi = sin(pi x1) sin(pi x2) (1 + t) e^{-it} */
+#define ST_EXACT_PAPER 1  /* psi = e^{it} sin(pi x1) sin(pi x2) sin(t x1 x2), the paper's example */
+
+/* Space-time errors of a discrete solution (Section 4): out[0] = ||psi - psi_h||_{L2(Q)},
+ * out[1] = |psi - psi_h|_{H1(Q)} = (||d_t e||^2 + ||grad_x e||^2)^{1/2}, psi_h the trial-space
+ * function with nodal values psi0 at t_0 (device n_x c128, NULL = 0) and psi at t_1.. (device
+ * (n_t, n_x) c128).  Tensor quadrature per prism: q_t Gauss-Legendre points in time, q_x x q_x
+ * collapsed Gauss points per triangle (0 = 4; at most 8).  out: host double[2]; synchronous on
+ * `stream`.  ST_ERR_UNSUPPORTED for more than 65535 time elements. */
+st_status st_error_norms(st_fdm* h, int exact, const void* psi, const void* psi0, int q_t, int q_x,
+                         double* out, void* stream);
+
+/* Load vector of the manufactured right-hand side f = i d_t psi - Laplace psi by quadrature:
+ * F[k, a] = int_Q f phi_k varphi_a for the time DOFs t_1.. and interior nodes (eq. LGS right-hand
+ * side before the lifting), F device (n_t, n_x) c128, rules as in st_error_norms.  Asynchronous.
+ * Assembly helper (the paper integrates f with a high-order rule). */
+st_status st_load_quadrature(st_fdm* h, int exact, int q_t, int q_x, void* F, void* stream);
+
 /* ------------------------------------------------------------------ allocation-free residual */
 /* The FP64 residual of st_residual, for callers that must not allocate device memory while
  * they run: code calling it inside a CUDA stream capture in global mode (where cudaMalloc is a

@@ -31,6 +31,9 @@ ST_MIXED = 2
 ST_REFINE_GMRES = 0
 ST_REFINE_CLASSIC = 1
 
+ST_EXACT_C1 = 0
+ST_EXACT_PAPER = 1
+
 ST_XFORM_Y = 0
 ST_XFORM_X = 1
 ST_XFORM_XT = 2
@@ -97,6 +100,8 @@ SIGNATURES = {
     "st_time_transform": (c_int, [c_void_p, c_int, c_int, c_void_p, c_void_p, c_void_p]),
     "st_spatial_solve": (c_int, [c_void_p, c_int, c_void_p, c_void_p, c_void_p]),
     "st_load_nodal": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p]),
+    "st_error_norms": (c_int, [c_void_p, c_int, c_void_p, c_void_p, c_int, c_int, ctypes.POINTER(c_double), c_void_p]),
+    "st_load_quadrature": (c_int, [c_void_p, c_int, c_int, c_int, c_void_p, c_void_p]),
     "st_residual_noalloc": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]),
     "st_destroy_time": (None, [c_void_p]),
     "st_destroy_space": (None, [c_void_p]),

@@ -111,6 +111,8 @@ void free_handle(st_fdm* h) {
     cudaFree(h->dt.BTb);
     cudaFree(h->dt.Mfull0);
     cudaFree(h->dt.m);
+    cudaFree(h->dt.nodes);
+    cudaFree(h->ws_norm);
     cudaFree(h->ws_big);
     cudaFree(h->ws_g32);
     cudaFree(h->ws_win);
@@ -789,6 +791,8 @@ extern "C" st_status st_fdm_setup(const st_time* t, const st_space* sp, const st
     if (s == ST_OK) s = upload(&h->dt.BTb, BT.data(), (size_t)n * 5 * sizeof(double), "B_t^T band");
     if (s == ST_OK) s = upload(&h->dt.Mfull0, h->tm.Mfull0.data(), (size_t)n * sizeof(double), "M_t col 0");
     if (s == ST_OK) s = upload(&h->dt.m, h->tm.m.data(), (size_t)n * sizeof(double), "m_t");
+    if (s == ST_OK)
+        s = upload(&h->dt.nodes, h->tm.nodes.data(), h->tm.nodes.size() * sizeof(double), "time mesh nodes");
     if (s == ST_OK) {
         size_t parts = (size_t)residual_num_partials(n, h->sm.n_x);
         s = grow(*reinterpret_cast<void**>(&h->ws_red), h->ws_red_bytes, (8 + 2 * parts) * sizeof(double), "reduction");

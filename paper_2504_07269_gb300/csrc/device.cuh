@@ -53,6 +53,7 @@ struct DevTime {
     double* BTb = nullptr;    // n_t x 5 band of B_t^T
     double* Mfull0 = nullptr; // full M_t rows 1..n_t, column t_0
     double* m = nullptr;      // m_t
+    double* nodes = nullptr;  // time mesh nodes t_0 .. t_N
 };
 
 // which transform matrix
@@ -218,6 +219,8 @@ struct st_fdm {
     float* tc_bt = nullptr;       // [2][N2_pad][K_pad]
     size_t tc_bt_bytes = 0;
     CUtensorMap tc_mapB;
+    void* ws_norm = nullptr;      // error-norm partial sums
+    size_t ws_norm_bytes = 0;
     int factors_valid = 0;        // ws_L holds the factors of all n_t systems (keep mode)
     int factors_prec = -1;
 };

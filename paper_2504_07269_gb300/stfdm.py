@@ -348,6 +348,29 @@ def st_load_nodal(h: FdmHandle, f_nodal, F=None, stream=None):
     return F
 
 
+EXACT = {"c1": _lib.ST_EXACT_C1, "paper": _lib.ST_EXACT_PAPER}
+
+
+def st_error_norms(h: FdmHandle, exact: str, psi, psi0=None, q_t: int = 0, q_x: int = 0, stream=None):
+    """(L2(Q) error, H1(Q) seminorm error) of the trial-space function with nodal values psi0 (t_0)
+    and psi (t_1..) against the manufactured solution `exact` ("c1" or "paper")."""
+    _check_st(h, psi, torch.complex128, "psi")
+    _check_vec(h, psi0, torch.complex128, "psi0")
+    out = (ctypes.c_double * 2)()
+    check(lib().st_error_norms(h.ptr, EXACT[exact], _ptr(psi), _ptr(psi0), int(q_t), int(q_x), out, _stream(stream)),
+          "st_error_norms")
+    return out[0], out[1]
+
+
+def st_load_quadrature(h: FdmHandle, exact: str, F=None, q_t: int = 0, q_x: int = 0, stream=None):
+    if F is None:
+        F = torch.empty((h.n_t, h.n_x), dtype=torch.complex128, device=torch.device("cuda", torch.cuda.current_device()))
+    _check_st(h, F, torch.complex128, "F")
+    check(lib().st_load_quadrature(h.ptr, EXACT[exact], int(q_t), int(q_x), _ptr(F), _stream(stream)),
+          "st_load_quadrature")
+    return F
+
+
 def st_residual_noalloc(h: FdmHandle, F, psi0, psi, R, norms, stream=None):
     """Allocation-free residual: writes R (or nothing if R is None) and norms[0:2] =
     (||R||^2, ||F~||^2) into caller-provided device tensors; never synchronises."""

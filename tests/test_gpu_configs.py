@@ -1,0 +1,141 @@
+"""Full-size checks of the other configurations (each in a fresh module, so that no handle of
+the 256x256 benchmark workload holds device memory meanwhile):
+  * 384x384 squares, P2 time n_t = 1024, T = 2, packet initial value, mixed precision;
+  * 128x128 squares, P1 time N_t = 256, adjoint source control: gradient vs finite differences.
+"""
+import numpy as np
+import pytest
+import scipy.sparse as sp
+import scipy.sparse.linalg as spla
+
+import synth
+from oracle import fe_space, fe_time, solve
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+# ------------------------------------------------------------------ 384x384 squares, P2 time (n_t = 1024)
+def test_c3_mixed_p2_packets():
+    """384x384 squares P1 (146,689 nodes, b = 384), P2 time on 512 elements (n_t = 1024), T = 2,
+    psi0 = four seeded packets, f = 0: 150,209,536 unknowns.  The factors (463 GB) do not fit, so
+    every FP32 application refactorises.  Checks at this size: the oracle's FP64 residual of the
+    mixed solution meets the 1e-10 target, and sampled spatial solves agree with SuperLU."""
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import time
+
+    from paper_2504_07269_gb300 import build, stfdm
+
+    build.build()
+    torch.cuda.empty_cache()
+    dev = torch.device("cuda:0")
+    pr = synth.config_problem("c3")
+    t0 = time.perf_counter()
+    h = stfdm.setup_problem(pr.n, pr.p_t, pr.t_nodes, device=0)
+    t1 = time.perf_counter()
+    x1, x2 = synth.interior_coords(pr.n)
+    psi0 = synth.packet_values(synth.packet_params(pr.seed), x1, x2)
+    F = torch.zeros((h.n_t, h.n_x), dtype=torch.complex128, device=dev)
+    p0 = torch.from_numpy(psi0).to(dev)
+    torch.cuda.synchronize()
+    t2 = time.perf_counter()
+    # the restart length follows the free memory; allow for slower restarted convergence
+    psi, info = stfdm.st_fdm_solve(h, F, p0, precision="mixed", tol=1e-10, max_sweeps=80)
+    torch.cuda.synchronize()
+    t3 = time.perf_counter()
+    print(f"c3: setup {t1 - t0:.1f} s (kappa_X {h.kappa:.2e}), mixed solve {t3 - t2:.1f} s = "
+          f"{pr.unknowns / (t3 - t2):.3e} unknowns/s, sweeps {info['sweeps']}, factors kept {info['factors_kept']}, "
+          f"residual {info['rel_residual']:.2e}")
+    M_t, B_t, m_t, _ = fe_time.assemble_time(pr.p_t, pr.t_nodes)
+    M_x, A_x = fe_space.assemble_space(pr.n)
+    U = psi.cpu().numpy()
+    Ft = -np.outer(m_t, A_x @ psi0)
+    _, r = solve.residual(M_t, B_t, M_x, A_x, U - psi0[None, :], Ft)
+    print(f"c3 oracle residual {r:.2e}")
+    assert r <= 1e-10
+    del psi, U
+    # sampled spatial solves at this size (b = 384)
+    _, s, _, _ = stfdm.st_time_decompose(h.time)
+    G = synth.cn01((h.n_t, h.n_x), seed=78)
+    W32 = stfdm.st_spatial_solve(h, "fp32", torch.from_numpy(G).to(dev).to(torch.complex64)).cpu().numpy()
+    # FP32 pivot-free LDL^T: backward error at the FP32 level; forward error ~ cond(C_k) u_32, and
+    # cond(M_x + s_k A_x) reaches ~1e5 at b = 384 for the largest |s_k| (k = 0)
+    for k in (0, h.n_t // 2, h.n_t - 1):
+        C = sp.csc_matrix(M_x + s[k] * A_x, dtype=np.complex128)
+        ref = spla.splu(C).solve(G[k])
+        e = np.linalg.norm(W32[k] - ref) / np.linalg.norm(ref)
+        be = np.linalg.norm(C @ W32[k] - G[k]) / (spla.norm(C, 1) * np.linalg.norm(W32[k]))
+        print(f"c3 spatial solve k={k}: fp32 rel. error {e:.2e}, normwise backward error {be:.2e}")
+        assert be <= 1e-5
+        assert e <= 5e-2
+
+
+# ------------------------------------------------------------------ 128x128 squares, adjoint source control
+def test_c4_adjoint_gradient_vs_finite_differences():
+    """J(f) = 1/2 ||psi_h(f) - psi_target||^2_W + alpha/2 ||f||^2_W, W = M_t (x) M_x, F = W f,
+    alpha = 1e-3, target and psi0 seeded packets (128x128 squares, P1 time N_t = 256, T = 1).
+    The gradient W K^{-H} W e + alpha W f (one adjoint solve) against central differences of J
+    (two FP64 forward solves each) along 20 seeded complex directions (|d| = |f|).  J is quadratic
+    in f, so the difference quotient has no truncation error for any step: at h = 1e-3 it checks
+    the gradient to 1e-6; at h = 1e-6 the forward solves' rounding (about 1e-11 relative) is
+    amplified by 1/h, which bounds the agreement near 1e-5 (measured and reported)."""
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2504_07269_gb300 import build, stfdm
+
+    build.build()
+    dev = torch.device("cuda:0")
+    pr = synth.config_problem("c4")
+    h = stfdm.setup_problem(pr.n, pr.p_t, pr.t_nodes, device=0)
+    M_t, B_t, m_t, _ = fe_time.assemble_time(pr.p_t, pr.t_nodes)
+    M_x, A_x = fe_space.assemble_space(pr.n)
+    x1, x2 = synth.interior_coords(pr.n)
+    target = synth.packet_values(synth.packet_params(pr.seed + 1), x1, x2)[None, :]
+    psi0 = synth.packet_values(synth.packet_params(pr.seed), x1, x2)
+    p0 = torch.from_numpy(psi0).to(dev)
+    alpha = 1e-3
+
+    def W(v):                                   # (M_t (x) M_x) v for an (n_t, n_x) array
+        return M_t @ (M_x @ v.T).T
+
+    def wdot(a, b):                             # a^H W b
+        return np.vdot(a, W(b))
+
+    def forward(f, precision="fp64"):
+        psi, _ = stfdm.st_fdm_solve(h, torch.from_numpy(W(f)).to(dev), p0, precision=precision)
+        return psi.cpu().numpy()
+
+    def J(f):
+        e = forward(f) - target
+        return 0.5 * wdot(e, e).real + 0.5 * alpha * wdot(f, f).real
+
+    f = synth.cn01((h.n_t, h.n_x), seed=pr.seed + 2)
+    e = forward(f) - target
+    lam, _ = stfdm.st_adjoint_solve(h, torch.from_numpy(W(e)).to(dev), precision="fp64")
+    g = W(lam.cpu().numpy()) + alpha * W(f)
+    dirs = []
+    for i in range(20):
+        d = synth.cn01(f.shape, seed=1000 + i)
+        dirs.append(d * (np.linalg.norm(f) / np.linalg.norm(d)))
+    for hstep, ndir, bar in ((1e-3, 20, 1e-6), (1e-6, 5, 1e-4)):
+        gaps = []
+        for d in dirs[:ndir]:
+            fd = (J(f + hstep * d) - J(f - hstep * d)) / (2 * hstep)
+            ad = np.vdot(g, d).real
+            gaps.append(abs(fd - ad) / abs(ad))
+        print(f"c4 adjoint gradient vs central differences, h = {hstep:g} ({ndir} directions): relative gaps "
+              f"max {max(gaps):.2e}, median {np.median(gaps):.2e}")
+        assert max(gaps) <= bar
+    # the mixed-precision adjoint (FP32 FDM refined by FP64 GMRES) against the FP64 adjoint
+    try:
+        lam32, info = stfdm.st_adjoint_solve(h, torch.from_numpy(W(e)).to(dev), precision="mixed", tol=1e-11,
+                                             max_sweeps=60)
+    except Exception as ex:
+        print("c4 mixed adjoint:", ex, getattr(ex, "info", None))
+        raise
+    g32 = W(lam32.cpu().numpy()) + alpha * W(f)
+    gdiff = np.linalg.norm(g32 - g) / np.linalg.norm(g)
+    print(f"c4 gradient, mixed-precision adjoint vs FP64 adjoint: {gdiff:.2e} "
+          f"(sweeps {info['sweeps']}, residual history {info['residual_history']})")
+    assert gdiff <= 1e-8
