@@ -375,10 +375,10 @@ __device__ __forceinline__ void band_factor_v4(const BandArgs<float>& a, const f
             if (sq >= WR) sq -= WR;
             z[c0 + tid] = cmul<T>(zb[sq], dinv[tid]);
         }
-        // 5. trailing update, items of 8 rows x 64 columns, 2 columns per lane.  The complex
-        //    products run on packed FP32 pairs (two FMAs per instruction): with a = d_q L(c, q),
-        //    acc += p (-a.x, -a.x) and acx += p (a.y, a.y) for the row entries p = L(r, q); the
-        //    updated entry is (acc.x + acx.y, acc.y - acx.x).
+        // 5. trailing update, items of 8 rows x 64 columns, 2 columns per lane: the panel's products
+        //    sum_q L(r, q) d_q L(c, q) are accumulated on their own and subtracted from the window
+        //    entry once (the entries are loaded before the sum, hiding their latency), which rounds
+        //    less than updating the entry term by term.
         {
             const int R6 = rows_p - nbk;
             const int ngroups = (R6 + 7) >> 3;
@@ -386,24 +386,24 @@ __device__ __forceinline__ void band_factor_v4(const BandArgs<float>& a, const f
                 const int rr0 = rg * 8;
                 const int nseg = (rr0 + 7) / 64 + 1;
                 const int jmax = min(7, WR - 1 - nbk - rr0);
-                size_t rowb[8];
+                int rowb[8];   // window offsets of the 8 rows (< WR WB)
 #pragma unroll
                 for (int j = 0; j < 8; ++j) {
                     int sl = rbase + nbk + rr0 + j;
                     while (sl >= WR) sl -= WR;
-                    rowb[j] = (size_t)sl * WB;
+                    rowb[j] = sl * WB;
                 }
                 for (int cs = 0; cs < nseg; ++cs) {
                     const int cc0 = cs * 64 + lane, cc1 = cc0 + 32;
                     const bool act1 = (cs * 64 + 32) <= (rr0 + 7);   // second sub-block touches the triangle
-                    float2 acc[8][2], acx[8][2];
+                    float2 acc[8][2], wv[8][2];
 #pragma unroll
                     for (int j = 0; j < 8; ++j) {
                         const int rr = rr0 + j;
-                        acc[j][0] = (rr < R6 && cc0 <= rr) ? W[rowb[j] + (rr - cc0)] : mk<T>(0, 0);
-                        acc[j][1] = (act1 && rr < R6 && cc1 <= rr) ? W[rowb[j] + (rr - cc1)] : mk<T>(0, 0);
-                        acx[j][0] = mk<T>(0, 0);
-                        acx[j][1] = mk<T>(0, 0);
+                        wv[j][0] = (rr < R6 && cc0 <= rr) ? W[rowb[j] + (rr - cc0)] : mk<T>(0, 0);
+                        wv[j][1] = (act1 && rr < R6 && cc1 <= rr) ? W[rowb[j] + (rr - cc1)] : mk<T>(0, 0);
+                        acc[j][0] = mk<T>(0, 0);
+                        acc[j][1] = mk<T>(0, 0);
                     }
                     const int ci0 = min(nbk + cc0, WR - 1), ci1 = min(nbk + cc1, WR - 1);
                     if (act1) {
@@ -412,39 +412,28 @@ __device__ __forceinline__ void band_factor_v4(const BandArgs<float>& a, const f
                             const float2 dq = P[q * WR + q];
                             const float2 a0 = cmul<T>(P[q * WR + ci0], dq);
                             const float2 a1 = cmul<T>(P[q * WR + ci1], dq);
-                            const float2 r0 = make_float2(-a0.x, -a0.x), i0 = make_float2(a0.y, a0.y);
-                            const float2 r1 = make_float2(-a1.x, -a1.x), i1 = make_float2(a1.y, a1.y);
                             const float2* prow = P + q * WR + nbk + rr0;
 #pragma unroll
                             for (int j = 0; j < 8; ++j) {
                                 const float2 pv = prow[min(j, jmax)];
-                                acc[j][0] = __ffma2_rn(pv, r0, acc[j][0]);
-                                acx[j][0] = __ffma2_rn(pv, i0, acx[j][0]);
-                                acc[j][1] = __ffma2_rn(pv, r1, acc[j][1]);
-                                acx[j][1] = __ffma2_rn(pv, i1, acx[j][1]);
+                                cfma<T>(acc[j][0], pv, a0);
+                                cfma<T>(acc[j][1], pv, a1);
                             }
                         }
                     } else {
 #pragma unroll 2
                         for (int q = 0; q < nbk; ++q) {
                             const float2 a0 = cmul<T>(P[q * WR + ci0], P[q * WR + q]);
-                            const float2 r0 = make_float2(-a0.x, -a0.x), i0 = make_float2(a0.y, a0.y);
                             const float2* prow = P + q * WR + nbk + rr0;
 #pragma unroll
-                            for (int j = 0; j < 8; ++j) {
-                                const float2 pv = prow[min(j, jmax)];
-                                acc[j][0] = __ffma2_rn(pv, r0, acc[j][0]);
-                                acx[j][0] = __ffma2_rn(pv, i0, acx[j][0]);
-                            }
+                            for (int j = 0; j < 8; ++j) cfma<T>(acc[j][0], prow[min(j, jmax)], a0);
                         }
                     }
 #pragma unroll
                     for (int j = 0; j < 8; ++j) {
                         const int rr = rr0 + j;
-                        if (rr < R6 && cc0 <= rr)
-                            W[rowb[j] + (rr - cc0)] = mk<T>(acc[j][0].x + acx[j][0].y, acc[j][0].y - acx[j][0].x);
-                        if (act1 && rr < R6 && cc1 <= rr)
-                            W[rowb[j] + (rr - cc1)] = mk<T>(acc[j][1].x + acx[j][1].y, acc[j][1].y - acx[j][1].x);
+                        if (rr < R6 && cc0 <= rr) W[rowb[j] + (rr - cc0)] = csub<T>(wv[j][0], acc[j][0]);
+                        if (act1 && rr < R6 && cc1 <= rr) W[rowb[j] + (rr - cc1)] = csub<T>(wv[j][1], acc[j][1]);
                     }
                 }
             }
