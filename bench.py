@@ -516,20 +516,9 @@ def run_batch(args):
     e2e_ms = reduce_max(e0.elapsed_time(e1) / args.steps, world, dev)
     h2d = sum(x.numel() * x.element_size() for x in Fh + P0h)
     d2h = sum(x.numel() * x.element_size() for x in Ph)
-    # residual of every problem (FP64, separate kernel) and the error of three against the FP64 FDM
+    # residual of every problem (FP64, separate kernel)
     stfdm.st_batch_solve(b, Fs, P0, psis, want_info=False)
     worst_res = max(stfdm.st_residual(h, F, p, o)[0] for h, F, p, o in zip(hs, Fs, P0, psis))
-    errs = {}
-    fp64_s = 0.0
-    if not args.no_fp64_check:
-        sizes = [pr.unknowns for pr in probs]
-        for i in sorted({int(np.argmax(sizes)), int(np.argmin(sizes)), int(np.argsort(sizes)[len(sizes) // 2])}):
-            torch.cuda.synchronize()
-            ta = time.perf_counter()
-            ref, _ = stfdm.st_fdm_solve(hs[i], Fs[i], P0[i], precision="fp64")
-            torch.cuda.synchronize()
-            fp64_s += time.perf_counter() - ta
-            errs[i] = float(torch.linalg.vector_norm(psis[i] - ref) / torch.linalg.vector_norm(ref))
     # dominant kernel: the persistent factor-and-solve over all 26,570 systems
     times = []
     for _ in range(3):
@@ -541,6 +530,22 @@ def run_batch(args):
         times.append(e0.elapsed_time(e1) * 1e-3)
     tk = statistics.median(times)
     flops = sum(8.0 * pr.n_t * pr.n_x * pr.n * pr.n / 2.0 for pr in probs)   # b = n per problem
+    # the plan's workspace (kept factors included) is released before the FP64 reference solves
+    stfdm.st_destroy_batch(b)
+    torch.cuda.synchronize()
+    # the error of three problems against the FP64 FDM
+    errs = {}
+    fp64_s = 0.0
+    if not args.no_fp64_check:
+        sizes = [pr.unknowns for pr in probs]
+        for i in sorted({int(np.argmax(sizes)), int(np.argmin(sizes)), int(np.argsort(sizes)[len(sizes) // 2])}):
+            torch.cuda.synchronize()
+            ta = time.perf_counter()
+            ref, _ = stfdm.st_fdm_solve(hs[i], Fs[i], P0[i], precision="fp64")
+            torch.cuda.synchronize()
+            fp64_s += time.perf_counter() - ta
+            errs[i] = float(torch.linalg.vector_norm(psis[i] - ref) / torch.linalg.vector_norm(ref))
+            del ref
     props = torch.cuda.get_device_properties(dev)
     max_mhz = (clocks or {}).get("sm_max_mhz") or (measured_peaks() or {}).get("sm_max_mhz", 2070.0)
     peak = props.multi_processor_count * 128 * 2 * max_mhz * 1e6 / 1e12

@@ -121,7 +121,7 @@ typedef struct {
 const char* st_status_string(st_status s);
 const char* st_last_error_message(void);
 int st_abi_version(void);   /* returns STFDM_ABI_VERSION of the built library */
-#define STFDM_ABI_VERSION 2
+#define STFDM_ABI_VERSION 3
 
 /* ------------------------------------------------------------------ assembly (host) */
 /* Temporal matrices of eq. (matrix_t), Section 3.  p_t in {1, 2}: continuous piecewise
@@ -211,8 +211,9 @@ st_status st_fdm_solve_batched(st_fdm* const* hs, int count, const void* const* 
  *   - an autotuner times the candidate transform tile shapes and CTAs per SM of the spatial solve
  *     on the plan's data at creation and keeps the fastest (cached per shape signature).
  * The plan owns its workspace: the GMRES basis ((m+1) complex128 + m complex64 vectors of the
- * packed length), one factor slot per resident CTA (no factors are kept between applications),
- * the transform buffer.  Solves on one plan must not overlap; the handles must outlive the plan.
+ * packed length), one factor slot per resident CTA, the transform buffer, and -- unless
+ * opts->no_keep -- kept LDL^T factors for the problems with the widest bands (b <= 256) that fit in
+ * the free memory left at creation: their later applications only run the substitutions.  Solves on one plan must not overlap; the handles must outlive the plan.
  * The paper solves one problem at a time; batching is an extension. */
 typedef struct st_batch st_batch;
 
@@ -222,6 +223,7 @@ typedef struct {
     int restart;       /* GMRES restart length m, 0 = automatic (<= 20, basis within half the free memory) */
     int no_graph;      /* 1: launch each cycle directly instead of replaying a captured CUDA graph */
     int no_tune;       /* 1: skip the autotuner (square 64 x 64 transform tiles, maximum CTAs per SM) */
+    int no_keep;       /* 1: refactorise every spatial system at every preconditioner application */
 } st_batch_opts;
 
 typedef struct {
@@ -237,6 +239,8 @@ typedef struct {
     double tune_seconds;       /* time spent tuning */
     long long unknowns;        /* total space-time unknowns */
     unsigned long long workspace_bytes;
+    int kept_problems;         /* problems whose LDL^T factors are kept across applications */
+    unsigned long long kept_factor_bytes;
 } st_batch_stats;
 
 /* Builds the plan and, unless opts->no_tune, runs the autotuner on the device (synchronous).

@@ -57,14 +57,15 @@ class st_solve_info(ctypes.Structure):
 
 class st_batch_opts(ctypes.Structure):
     _fields_ = [("tol", c_double), ("max_sweeps", c_int), ("restart", c_int), ("no_graph", c_int),
-                ("no_tune", c_int)]
+                ("no_tune", c_int), ("no_keep", c_int)]
 
 
 class st_batch_stats(ctypes.Structure):
     _fields_ = [("count", c_int), ("items", c_int), ("restart", c_int), ("xform_tile_m", c_int),
                 ("xform_tile_n", c_int), ("solve_ctas_per_sm", c_int), ("solve_grid", c_int),
                 ("graph_nodes", c_int), ("cycles", c_int), ("tuned", c_int), ("tune_seconds", c_double),
-                ("unknowns", ctypes.c_longlong), ("workspace_bytes", ctypes.c_ulonglong)]
+                ("unknowns", ctypes.c_longlong), ("workspace_bytes", ctypes.c_ulonglong),
+                ("kept_problems", c_int), ("kept_factor_bytes", ctypes.c_ulonglong)]
 
 
 # name -> (restype, argtypes); every entry point declared in include/stfdm.h

@@ -54,6 +54,7 @@ cudaError_t kb_launch_init(const BatchGm& gm, int P, int m, cudaStream_t st);
 cudaError_t kb_launch_cycle_start(const BatchGm& gm, int P, int m, double tol, int maxit, cudaStream_t st);
 cudaError_t kb_launch_arnoldi(const BatchGm& gm, int P, int m, int j, double tol, int maxit, cudaStream_t st);
 cudaError_t kb_launch_solve_y(const BatchGm& gm, int P, int m, cudaStream_t st);
+cudaError_t kb_launch_mark_factored(const BatchBand* probs, const int* active, int* factored, int P, cudaStream_t st);
 cudaError_t launch_stencil_A(const SpaceMats& sm, const void* in, bool in_c64, const double2* add, double sign,
                              double2* out, cudaStream_t st);
 cudaError_t launch_add_row(int n_t, int n_x, void* psi, const void* psi0, bool c64, cudaStream_t st);
@@ -140,6 +141,13 @@ struct st_batch {
     float2* Lslots = nullptr;
     float2* Dslots = nullptr;
     int* counter = nullptr;
+    int* factored = nullptr;  // per problem: kept factors stored (set after its first application)
+    int2* d_kitems = nullptr; // work list of the kept-factor systems
+    int n_kitems = 0;
+    int kept = 0;             // problems with kept factors
+    int kb_max = 0;           // widest band among them
+    size_t kept_bytes = 0;
+    std::vector<BatchBand> hband;
     int* status = nullptr;
     void* gm_mem = nullptr;
     BatchGm gm{};
@@ -201,8 +209,16 @@ cudaError_t enqueue_cycle(st_batch* b, cudaStream_t st) {
         double2* Vj = b->V + (size_t)j * N;
         float2* Zj = b->Z + (size_t)j * N;
         BQ(kb_launch_xform(shape, b->ntiles[shape], b->d_prob, tile0_of(b, shape), P, gm.active, 0, Vj, true, b->G, st));
-        BQ(band_batch_launch(b->d_band, b->d_items, b->n_items, gm.active, b->counter, b->b_max, b->win, b->Lslots,
-                             b->L_stride, b->Dslots, b->D_stride, b->status, b->grid, st));
+        BQ(band_batch_launch(b->d_band, b->d_items, b->n_items, gm.active, b->factored, b->counter, b->b_max, b->win,
+                             b->Lslots, b->L_stride, b->Dslots, b->D_stride, b->status, b->grid, st));
+        if (b->n_kitems > 0) {
+            // systems whose factors are kept from an earlier application: substitutions only
+            BQ(subst_batch_launch(b->d_band, b->d_kitems, b->n_kitems, gm.active, b->factored, b->kb_max, b->status,
+                                  true, st));
+            BQ(subst_batch_launch(b->d_band, b->d_kitems, b->n_kitems, gm.active, b->factored, b->kb_max, b->status,
+                                  false, st));
+            BQ(kb_launch_mark_factored(b->d_band, gm.active, b->factored, P, st));
+        }
         BQ(kb_launch_xform(shape, b->ntiles[shape], b->d_prob, tile0_of(b, shape), P, gm.active, 1, b->G, false, Zj, st));
         BQ(kb_launch_apply(b->n_res, b->d_prob, b->d_res0, P, gm.active, Zj, b->w, st));
         for (int pass = 0; pass < 2; ++pass) {
@@ -292,7 +308,7 @@ st_status tune(st_batch* b) {
         float tms[3] = {0, 0, 0};
         for (int c = 1; c <= 2; ++c) {
             st_status r = time_ms(st, [&]() {
-                return band_batch_launch(b->d_band, b->d_items, sample, b->gm.active, b->counter, b->b_max, b->win,
+                return band_batch_launch(b->d_band, b->d_items, sample, b->gm.active, nullptr, b->counter, b->b_max, b->win,
                                          b->Lslots, b->L_stride, b->Dslots, b->D_stride, b->status, c * b->sm_count, st);
             }, &tms[c]);
             if (r != ST_OK) return r;
@@ -493,6 +509,7 @@ extern "C" st_status st_batch_create(st_fdm* const* hs, int count, const st_batc
     BA(Dslots, (size_t)b->grid * max_nx * sizeof(float2), "pivot slots");
     BA(counter, sizeof(int), "work counter");
     BA(status, 2 * sizeof(int), "status");
+    BA(factored, sizeof(int) * P, "factor flags");
 #undef BA
     {
         // per-problem GMRES state, carved out of one allocation (every array 16-byte aligned);
@@ -534,6 +551,61 @@ extern "C" st_status st_batch_create(st_fdm* const* hs, int count, const st_batc
         layout(static_cast<char*>(b->gm_mem));
     }
     for (int q = 0; q < P; ++q) band[q].rhs = b->G + b->off[q];
+    // Kept factors: problems with the widest bands first (the factorisation costs n_x b^2 per system,
+    // its storage n_x b), as long as they fit in the free memory left (less a reserve); their later
+    // preconditioner applications only stream the factors (grouped substitutions, b <= 256).
+    std::vector<int2> kitems;
+    if (!o.no_keep) {
+        size_t freeb = 0, total = 0;
+        cudaMemGetInfo(&freeb, &total);
+        const size_t reserve = (size_t)2 << 30;
+        size_t budget = freeb > reserve ? (size_t)((freeb - reserve) * 0.9) : 0;
+        std::vector<int> order(P);
+        for (int q = 0; q < P; ++q) order[q] = q;
+        std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return band[x].b > band[y].b; });
+        std::vector<size_t> loff(P, 0);
+        size_t need = 0;
+        std::vector<char> keep(P, 0);
+        for (int q : order) {
+            if (band[q].b > 256) continue;
+            const size_t nt = (size_t)hs[q]->tm.n_t, nx = (size_t)band[q].n;
+            // L then D; each problem's block 256-byte aligned (the bulk copies need 16-byte sources)
+            const size_t bytes = (nt * nx * ((size_t)band[q].b + 1) * sizeof(float2) + 255) / 256 * 256;
+            if (need + bytes > budget) continue;
+            keep[q] = 1;
+            loff[q] = need;
+            need += bytes;
+        }
+        if (need > 0) {
+            void* pk = nullptr;
+            s = balloc(b, &pk, need, "kept factors");
+            if (s == ST_OK) {
+                float2* base = static_cast<float2*>(pk);
+                for (int q = 0; q < P; ++q) {
+                    if (!keep[q]) continue;
+                    const size_t nt = (size_t)hs[q]->tm.n_t, nx = (size_t)band[q].n;
+                    band[q].Lkeep = base + loff[q] / sizeof(float2);
+                    band[q].Dkeep = band[q].Lkeep + nt * nx * band[q].b;
+                    ++b->kept;
+                    b->kb_max = std::max(b->kb_max, band[q].b);
+                }
+                b->kept_bytes = need;
+                for (const int2& it : items)
+                    if (keep[it.x]) kitems.push_back(it);
+            } else {
+                cudaGetLastError();   // not enough memory after all: refactorise everything
+                s = ST_OK;
+            }
+        }
+    }
+    b->n_kitems = (int)kitems.size();
+    if (b->n_kitems > 0) {
+        void* pk = nullptr;
+        s = balloc(b, &pk, sizeof(int2) * kitems.size(), "kept work list");
+        if (s != ST_OK) return bail(s);
+        b->d_kitems = static_cast<int2*>(pk);
+    }
+    b->hband = band;
     cudaStream_t st = b->cs;
     cudaError_t e = cudaMemcpyAsync(b->d_prob, b->hprob.data(), sizeof(BatchProb) * P, cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess) e = cudaMemcpyAsync(b->d_band, band.data(), sizeof(BatchBand) * P, cudaMemcpyHostToDevice, st);
@@ -543,6 +615,9 @@ extern "C" st_status st_batch_create(st_fdm* const* hs, int count, const st_batc
     if (e == cudaSuccess) e = cudaMemcpyAsync(b->d_seg0, seg0.data(), sizeof(int) * (P + 1), cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(b->d_tile0, tile0.data(), sizeof(int) * tile0.size(), cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess && b->n_kitems > 0)
+        e = cudaMemcpyAsync(b->d_kitems, kitems.data(), sizeof(int2) * kitems.size(), cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(b->factored, 0, sizeof(int) * P, st);
     if (e == cudaSuccess) e = cudaMemsetAsync(b->status, 0, 2 * sizeof(int), st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) return bail(fail(ST_ERR_CUDA, std::string("st_batch_create: upload: ") + cudaGetErrorString(e)));
@@ -590,6 +665,7 @@ extern "C" st_status st_batch_solve(st_batch* b, const void* const* F, const voi
     }
     BT_TRY(cudaMemcpyAsync(b->d_prob, b->hprob.data(), sizeof(BatchProb) * P, cudaMemcpyHostToDevice, st));
     BT_TRY(cudaMemsetAsync(b->status, 0, 2 * sizeof(int), st));
+    BT_TRY(cudaMemsetAsync(b->factored, 0, sizeof(int) * P, st));   // this call's right-hand sides: factor anew
     BT_TRY(kb_launch_init(b->gm, P, b->m, st));
     if (b->use_graph) {
         st_status s = build_graph(b);
@@ -652,7 +728,7 @@ extern "C" st_status st_batch_spatial_solve(st_batch* b, void* stream) {
     DevGuard guard(b->device);
     cudaStream_t us = reinterpret_cast<cudaStream_t>(stream);
     BT_TRY(cudaMemsetAsync(b->status, 0, 2 * sizeof(int), us));
-    BT_TRY(band_batch_launch(b->d_band, b->d_items, b->n_items, nullptr, b->counter, b->b_max, b->win, b->Lslots,
+    BT_TRY(band_batch_launch(b->d_band, b->d_items, b->n_items, nullptr, nullptr, b->counter, b->b_max, b->win, b->Lslots,
                              b->L_stride, b->Dslots, b->D_stride, b->status, b->grid, us));
     return ST_OK;
 }
@@ -685,6 +761,8 @@ extern "C" st_status st_batch_stats_get(const st_batch* b, st_batch_stats* out) 
     out->tune_seconds = b->tune_seconds;
     out->unknowns = b->N;
     out->workspace_bytes = (unsigned long long)b->bytes;
+    out->kept_problems = b->kept;
+    out->kept_factor_bytes = (unsigned long long)b->kept_bytes;
     return ST_OK;
 }
 

@@ -116,13 +116,17 @@ struct BatchBand {
     float Mc, Mw, Ms, Md, Ac, Aw, As, Ad;
     const float2* shifts;   // s_k of the problem
     float2* rhs;            // its (n_t, n) right-hand sides in, solutions out
+    float2* Lkeep;          // kept factors (n_t systems of n b entries) or NULL: refactorised per use
+    float2* Dkeep;          // kept pivots (n_t x n)
 };
 size_t band_batch_smem(int b_max);
 cudaError_t band_batch_prepare(int b_max);
 int band_batch_occupancy(int b_max);
-cudaError_t band_batch_launch(const BatchBand* probs, const int2* items, int n_items, const int* active, int* counter,
-                              int b_max, float2* win, float2* Lslots, size_t L_stride, float2* Dslots, size_t D_stride,
-                              int* status, int grid, cudaStream_t st);
+cudaError_t band_batch_launch(const BatchBand* probs, const int2* items, int n_items, const int* active,
+                              const int* factored, int* counter, int b_max, float2* win, float2* Lslots, size_t L_stride,
+                              float2* Dslots, size_t D_stride, int* status, int grid, cudaStream_t st);
+cudaError_t subst_batch_launch(const BatchBand* probs, const int2* items, int n_items, const int* active,
+                               const int* factored, int b_max, int* status, bool fwd, cudaStream_t st);
 
 // batched solve: per-problem descriptor and per-problem GMRES state (device arrays)
 struct BatchProb {

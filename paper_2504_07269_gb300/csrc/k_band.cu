@@ -540,22 +540,28 @@ __device__ __forceinline__ void band_bwd_cta(int n, int b, const float2* __restr
 // blocked-panel kernel (forward substitution fused) into its private factor slot and solves the
 // backward substitution itself.  Items of problems whose `active` flag is 0 are skipped.
 __global__ void __launch_bounds__(V4_THREADS, 2)
-k_band_batch_v4(const BatchBand* probs, const int2* items, int n_items, const int* active, int* counter, float2* win,
-                size_t win_stride, float2* Lslots, size_t L_stride, float2* Dslots, size_t D_stride, int* status) {
+k_band_batch_v4(const BatchBand* probs, const int2* items, int n_items, const int* active, const int* factored,
+                int* counter, float2* win, size_t win_stride, float2* Lslots, size_t L_stride, float2* Dslots,
+                size_t D_stride, int* status) {
     extern __shared__ __align__(16) char smem[];
     __shared__ int s_item;
     __shared__ BandArgs<float> s_args;   // the current item's geometry and stencil (keeps registers free)
     __shared__ float2 s_shift;
     __shared__ float2* s_z;
+    __shared__ float2* s_L;   // factor columns: the problem's kept storage or this CTA's slot
+    __shared__ float2* s_D;
     for (;;) {
         if (threadIdx.x == 0) {
             const int it = atomicAdd(counter, 1);
             int run = 0;
             if (it < n_items) {
                 const int2 pk = items[it];
-                run = (!active || active[pk.x]) ? 1 : 2;
+                const BatchBand& pb = probs[pk.x];
+                // skip problems that are not iterating, and kept factors that are already stored
+                // (their systems are solved by the grouped substitutions)
+                const bool skip = (active && !active[pk.x]) || (pb.Lkeep && factored && factored[pk.x]);
+                run = skip ? 2 : 1;
                 if (run == 1) {
-                    const BatchBand& pb = probs[pk.x];
                     s_args.n = pb.n;
                     s_args.m = pb.m;
                     s_args.b = pb.b;
@@ -564,6 +570,13 @@ k_band_batch_v4(const BatchBand* probs, const int2* items, int n_items, const in
                     s_args.status = status;
                     s_shift = pb.shifts[pk.y];
                     s_z = pb.rhs + (size_t)pk.y * pb.n;
+                    if (pb.Lkeep) {
+                        s_L = pb.Lkeep + (size_t)pk.y * pb.n * pb.b;
+                        s_D = pb.Dkeep + (size_t)pk.y * pb.n;
+                    } else {
+                        s_L = Lslots + (size_t)blockIdx.x * L_stride;
+                        s_D = Dslots + (size_t)blockIdx.x * D_stride;
+                    }
                 }
             }
             s_item = run;
@@ -572,25 +585,23 @@ k_band_batch_v4(const BatchBand* probs, const int2* items, int n_items, const in
         const int run = s_item;
         if (run == 0) break;
         if (run == 1) {
-            float2* Lk = Lslots + (size_t)blockIdx.x * L_stride;
-            band_factor_v4(s_args, s_shift, s_z, Lk, Dslots + (size_t)blockIdx.x * D_stride,
-                           win + (size_t)blockIdx.x * win_stride, smem);
+            band_factor_v4(s_args, s_shift, s_z, s_L, s_D, win + (size_t)blockIdx.x * win_stride, smem);
             __syncthreads();
-            band_bwd_cta(s_args.n, s_args.b, Lslots + (size_t)blockIdx.x * L_stride, s_z, smem);
+            band_bwd_cta(s_args.n, s_args.b, s_L, s_z, smem);
         }
         __syncthreads();
     }
 }
 
-cudaError_t band_batch_launch(const BatchBand* probs, const int2* items, int n_items, const int* active, int* counter,
-                              int b_max, float2* win, float2* Lslots, size_t L_stride, float2* Dslots, size_t D_stride,
-                              int* status, int grid, cudaStream_t st) {
+cudaError_t band_batch_launch(const BatchBand* probs, const int2* items, int n_items, const int* active,
+                              const int* factored, int* counter, int b_max, float2* win, float2* Lslots, size_t L_stride,
+                              float2* Dslots, size_t D_stride, int* status, int grid, cudaStream_t st) {
     const size_t smem = band_batch_smem(b_max);
     const size_t win_stride = (size_t)(b_max + V4_NB) * (b_max + 1);
     cudaError_t e = cudaMemsetAsync(counter, 0, sizeof(int), st);
     if (e != cudaSuccess) return e;
-    k_band_batch_v4<<<grid, V4_THREADS, smem, st>>>(probs, items, n_items, active, counter, win, win_stride, Lslots,
-                                                    L_stride, Dslots, D_stride, status);
+    k_band_batch_v4<<<grid, V4_THREADS, smem, st>>>(probs, items, n_items, active, factored, counter, win, win_stride,
+                                                    Lslots, L_stride, Dslots, D_stride, status);
     return cudaGetLastError();
 }
 

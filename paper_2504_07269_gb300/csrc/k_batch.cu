@@ -411,6 +411,12 @@ __global__ void kb_solve_y(BatchGm gm, int P, int m) {
     }
 }
 
+// a problem that iterated in this application and keeps its factors has them stored now
+__global__ void kb_mark_factored(const BatchBand* probs, const int* active, int* factored, int P) {
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p < P && probs[p].Lkeep && active[p]) factored[p] = 1;
+}
+
 // out_p = scale_p * T_p in_p for every masked-in problem, T_p = Y_t (which 0, scale psc) or X_t
 // (which 1, scale 1/psc); complex64 arithmetic and output, TB input (complex128 or complex64).
 // Tiles of BM time rows x BN spatial columns, 256 threads, (BM/16) x (BN/16) outputs per thread.
@@ -577,6 +583,11 @@ cudaError_t kb_launch_cycle_start(const BatchGm& gm, int P, int m, double tol, i
 
 cudaError_t kb_launch_arnoldi(const BatchGm& gm, int P, int m, int j, double tol, int maxit, cudaStream_t st) {
     kb_arnoldi<<<(P + 127) / 128, 128, 0, st>>>(gm, P, m, j, tol, maxit);
+    return cudaGetLastError();
+}
+
+cudaError_t kb_launch_mark_factored(const BatchBand* probs, const int* active, int* factored, int P, cudaStream_t st) {
+    kb_mark_factored<<<(P + 127) / 128, 128, 0, st>>>(probs, active, factored, P);
     return cudaGetLastError();
 }
 

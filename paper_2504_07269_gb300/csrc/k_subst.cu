@@ -41,19 +41,57 @@ struct SubShared {
     int consumed;    // stages released by the consumer
 };
 
+// One system for the substitution kernels: n rows, half bandwidth b, its factor columns L, pivots
+// D and right-hand side z (solution on exit); n = 0 marks an item to skip.
 template <typename T>
-__device__ __forceinline__ size_t subst_slot(const BandArgs<T>& a, int k, int ks) {
-    return a.keep ? (size_t)k : (size_t)ks;
-}
+struct SubSys {
+    int n, b;
+    const C<T>* L;
+    const C<T>* D;
+    C<T>* z;
+};
+
+// the systems k0 .. k0 + nsys - 1 of one problem
+template <typename T>
+struct SingleSrc {
+    BandArgs<T> a;
+    int k0, nsys;
+    __device__ int count() const { return nsys; }
+    __device__ SubSys<T> get(int ks) const {
+        const int k = k0 + ks;
+        const size_t slot = a.keep ? (size_t)k : (size_t)ks;
+        return SubSys<T>{a.n, a.b, a.L + slot * (size_t)a.n * a.b, a.D + slot * (size_t)a.n, a.rhs + (size_t)k * a.n};
+    }
+};
+
+// the kept-factor systems of a batch (work list of (problem, k)); items of problems that are not
+// iterating, or whose factors are not stored yet, are skipped
+struct GroupSrc {
+    const BatchBand* probs;
+    const int2* items;
+    int n_items;
+    const int* active;
+    const int* factored;
+    __device__ int count() const { return n_items; }
+    __device__ SubSys<float> get(int ks) const {
+        const int2 pk = items[ks];
+        const BatchBand& pb = probs[pk.x];
+        if ((active && !active[pk.x]) || !factored[pk.x] || !pb.Lkeep) return SubSys<float>{0, 0, nullptr, nullptr, nullptr};
+        return SubSys<float>{pb.n, pb.b, pb.Lkeep + (size_t)pk.y * pb.n * pb.b, pb.Dkeep + (size_t)pk.y * pb.n,
+                             pb.rhs + (size_t)pk.y * pb.n};
+    }
+};
 
 // Producer lane: the column groups of every system of this CTA, in the consumer's order.
 // Forward: groups [gG, gG + G) from the top; backward: the same G-aligned groups from the last.
-template <typename T, int G, bool FWD>
-__device__ void subst_produce(const BandArgs<T>& a, int k0, int nsys, C<T>* ring, SubShared* sh) {
-    const int n = a.n, b = a.b, ngroups = (n + G - 1) / G;
+// Stage s of the ring starts at s G sb entries (sb >= every system's b).
+template <typename T, int G, bool FWD, typename Src>
+__device__ void subst_produce(const Src& src, int sb, C<T>* ring, SubShared* sh) {
     int it = 0;
-    for (int ks = blockIdx.x; ks < nsys; ks += gridDim.x) {
-        const C<T>* L = a.L + subst_slot(a, k0 + ks, ks) * (size_t)n * b;
+    for (int ks = blockIdx.x; ks < src.count(); ks += gridDim.x) {
+        const SubSys<T> sys = src.get(ks);
+        if (sys.n == 0) continue;
+        const int n = sys.n, b = sys.b, ngroups = (n + G - 1) / G;
         for (int g = 0; g < ngroups; ++g, ++it) {
             const int s = it % SUB_STAGES;
             if (it >= SUB_STAGES &&
@@ -70,7 +108,7 @@ __device__ void subst_produce(const BandArgs<T>& a, int k0, int nsys, C<T>* ring
             const int cols = min(G, n - start);
             const uint32_t bytes = (uint32_t)((size_t)cols * b * sizeof(C<T>));   // n b is even: 16-byte multiple
             async::bar_expect_tx(&sh->full[s], bytes);
-            async::bulk_g2s(ring + (size_t)s * G * b, L + (size_t)start * b, bytes, &sh->full[s]);
+            async::bulk_g2s(ring + (size_t)s * G * sb, sys.L + (size_t)start * b, bytes, &sh->full[s]);
         }
     }
     sh->issued = it;
@@ -104,24 +142,24 @@ __device__ void subst_setup(SubShared* sh) {
 //      subtract L(r, c) z_c;
 //   2. every other row below the block subtracts sum_c L(r, c) z_c (independent accumulations);
 //   3. the block's y = z / d is stored; after the last block of a group the slots shift by one.
-template <typename T, int R, int G>
-__global__ void __launch_bounds__(64) k_subst_fwd(BandArgs<T> a, int k0, int nsys) {
+template <typename T, int R, int G, typename Src>
+__global__ void __launch_bounds__(64) k_subst_fwd(Src src, int sb, int* status) {
     extern __shared__ __align__(128) unsigned char smem_raw[];
-    const int n = a.n, b = a.b;
     C<T>* ring = reinterpret_cast<C<T>*>(smem_raw);
-    SubShared* sh = reinterpret_cast<SubShared*>(smem_raw + (size_t)SUB_STAGES * G * b * sizeof(C<T>));
+    SubShared* sh = reinterpret_cast<SubShared*>(smem_raw + (size_t)SUB_STAGES * G * sb * sizeof(C<T>));
     subst_setup<T, G>(sh);
     const int lane = threadIdx.x & 31;
     if (threadIdx.x >= 32) {
-        if (lane == 0) subst_produce<T, G, true>(a, k0, nsys, ring, sh);
+        if (lane == 0) subst_produce<T, G, true>(src, sb, ring, sh);
     } else {
-        const int ngroups = (n + G - 1) / G;
         int it = 0;
         bool ok = true;
-        for (int ks = blockIdx.x; ks < nsys && ok; ks += gridDim.x) {
-            const int k = k0 + ks;
-            C<T>* z = a.rhs + (size_t)k * n;
-            const C<T>* D = a.D + subst_slot(a, k, ks) * (size_t)n;
+        for (int ks = blockIdx.x; ks < src.count() && ok; ks += gridDim.x) {
+            const SubSys<T> sys = src.get(ks);
+            if (sys.n == 0) continue;
+            const int n = sys.n, b = sys.b, ngroups = (n + G - 1) / G;
+            C<T>* z = sys.z;
+            const C<T>* D = sys.D;
             C<T> zr[R + 1];
 #pragma unroll
             for (int t = 0; t <= R; ++t) {
@@ -138,7 +176,7 @@ __global__ void __launch_bounds__(64) k_subst_fwd(BandArgs<T> a, int k0, int nsy
                     ok = false;
                     break;
                 }
-                const C<T>* Ls = ring + (size_t)s * G * b;
+                const C<T>* Ls = ring + (size_t)s * G * sb;
                 const C<T> dg = dnext;
                 if (lane < G && j0 + G + lane < n) dnext = D[j0 + G + lane];   // the next block's pivots
                 const bool inblk = lane >= l0 && lane < l0 + G;
@@ -185,7 +223,7 @@ __global__ void __launch_bounds__(64) k_subst_fwd(BandArgs<T> a, int k0, int nsy
     __syncthreads();
     if (threadIdx.x == 0) {
         subst_drain(sh);
-        if (sh->err) atomicExch(a.status + 1, 1);
+        if (sh->err) atomicExch(status + 1, 1);
     }
 }
 
@@ -196,23 +234,23 @@ __global__ void __launch_bounds__(64) k_subst_fwd(BandArgs<T> a, int k0, int nsy
 //   2. the block's rows by a G-step chain from the top: w_c = y_c - partial_c - sum L(i, c) w_i
 //      over the block rows i > c;
 //   3. the block's w are stored; below the first block of a group the slots shift by one.
-template <typename T, int R, int G>
-__global__ void __launch_bounds__(64) k_subst_bwd(BandArgs<T> a, int k0, int nsys) {
+template <typename T, int R, int G, typename Src>
+__global__ void __launch_bounds__(64) k_subst_bwd(Src src, int sb, int* status) {
     extern __shared__ __align__(128) unsigned char smem_raw[];
-    const int n = a.n, b = a.b;
     C<T>* ring = reinterpret_cast<C<T>*>(smem_raw);
-    SubShared* sh = reinterpret_cast<SubShared*>(smem_raw + (size_t)SUB_STAGES * G * b * sizeof(C<T>));
+    SubShared* sh = reinterpret_cast<SubShared*>(smem_raw + (size_t)SUB_STAGES * G * sb * sizeof(C<T>));
     subst_setup<T, G>(sh);
     const int lane = threadIdx.x & 31;
     if (threadIdx.x >= 32) {
-        if (lane == 0) subst_produce<T, G, false>(a, k0, nsys, ring, sh);
+        if (lane == 0) subst_produce<T, G, false>(src, sb, ring, sh);
     } else {
-        const int ngroups = (n + G - 1) / G;
         int it = 0;
         bool ok = true;
-        for (int ks = blockIdx.x; ks < nsys && ok; ks += gridDim.x) {
-            const int k = k0 + ks;
-            C<T>* z = a.rhs + (size_t)k * n;  // y in, w out
+        for (int ks = blockIdx.x; ks < src.count() && ok; ks += gridDim.x) {
+            const SubSys<T> sys = src.get(ks);
+            if (sys.n == 0) continue;
+            const int n = sys.n, b = sys.b, ngroups = (n + G - 1) / G;
+            C<T>* z = sys.z;  // y in, w out
             C<T> wr[R + 1];
 #pragma unroll
             for (int t = 0; t <= R; ++t) wr[t] = mk<T>(0, 0);
@@ -228,7 +266,7 @@ __global__ void __launch_bounds__(64) k_subst_bwd(BandArgs<T> a, int k0, int nsy
                     break;
                 }
                 // the copy for this block starts at column j0 (see subst_produce)
-                const C<T>* Ls = ring + (size_t)s * G * b;
+                const C<T>* Ls = ring + (size_t)s * G * sb;
                 const C<T> yg = ynext;
                 if (lane < G && j0 - G + lane >= 0) ynext = z[j0 - G + lane];   // the next block's y
                 const bool inblk = lane >= l0 && lane < l0 + G && jb + lane < n;
@@ -287,31 +325,37 @@ __global__ void __launch_bounds__(64) k_subst_bwd(BandArgs<T> a, int k0, int nsy
     __syncthreads();
     if (threadIdx.x == 0) {
         subst_drain(sh);
-        if (sh->err) atomicExch(a.status + 1, 1);
+        if (sh->err) atomicExch(status + 1, 1);
     }
 }
 
-template <typename T, int R, int G>
-static cudaError_t launch_rg(const BandArgs<T>& a, int k0, int nsys, bool fwd, cudaStream_t st) {
-    const size_t smem = (size_t)SUB_STAGES * G * a.b * sizeof(C<T>) + sizeof(SubShared);
+template <typename T, int R, int G, typename Src>
+static cudaError_t launch_src(const Src& src, int count, int sb, int* status, bool fwd, cudaStream_t st) {
+    const size_t smem = (size_t)SUB_STAGES * G * sb * sizeof(C<T>) + sizeof(SubShared);
     int dev = 0, sms = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     if (e != cudaSuccess) return e;
     int occ = 0;
     if (fwd) {
-        e = cudaFuncSetAttribute(k_subst_fwd<T, R, G>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_subst_fwd<T, R, G>, 64, smem);
+        e = cudaFuncSetAttribute(k_subst_fwd<T, R, G, Src>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_subst_fwd<T, R, G, Src>, 64, smem);
     } else {
-        e = cudaFuncSetAttribute(k_subst_bwd<T, R, G>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_subst_bwd<T, R, G>, 64, smem);
+        e = cudaFuncSetAttribute(k_subst_bwd<T, R, G, Src>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_subst_bwd<T, R, G, Src>, 64, smem);
     }
     if (e != cudaSuccess) return e;
     if (occ < 1) return cudaErrorInvalidConfiguration;
-    const int blocks = std::min(nsys, occ * sms);
-    if (fwd) k_subst_fwd<T, R, G><<<blocks, 64, smem, st>>>(a, k0, nsys);
-    else k_subst_bwd<T, R, G><<<blocks, 64, smem, st>>>(a, k0, nsys);
+    const int blocks = std::max(1, std::min(count, occ * sms));
+    if (fwd) k_subst_fwd<T, R, G, Src><<<blocks, 64, smem, st>>>(src, sb, status);
+    else k_subst_bwd<T, R, G, Src><<<blocks, 64, smem, st>>>(src, sb, status);
     return cudaGetLastError();
+}
+
+template <typename T, int R, int G>
+static cudaError_t launch_rg(const BandArgs<T>& a, int k0, int nsys, bool fwd, cudaStream_t st) {
+    const SingleSrc<T> src{a, k0, nsys};
+    return launch_src<T, R, G, SingleSrc<T>>(src, nsys, a.b, a.status, fwd, st);
 }
 
 template <typename T>
@@ -341,6 +385,17 @@ cudaError_t subst_launch<float>(const BandArgs<float>& a, int k0, int nsys, bool
     if (R <= 8) return launch_rg<float, 8, 8>(a, k0, nsys, fwd, st);
     if (R <= 13) return launch_rg<float, 13, 4>(a, k0, nsys, fwd, st);
     if (R <= 16) return launch_rg<float, 16, 4>(a, k0, nsys, fwd, st);
+    return cudaErrorInvalidValue;
+}
+
+// grouped substitutions over the kept-factor systems of a batch (complex64; b <= 256)
+cudaError_t subst_batch_launch(const BatchBand* probs, const int2* items, int n_items, const int* active,
+                               const int* factored, int b_max, int* status, bool fwd, cudaStream_t st) {
+    if (n_items <= 0) return cudaSuccess;
+    const GroupSrc src{probs, items, n_items, active, factored};
+    const int R = (b_max + 31) / 32;
+    if (R <= 4) return launch_src<float, 4, 16, GroupSrc>(src, n_items, b_max, status, fwd, st);
+    if (R <= 8) return launch_src<float, 8, 8, GroupSrc>(src, n_items, b_max, status, fwd, st);
     return cudaErrorInvalidValue;
 }
 

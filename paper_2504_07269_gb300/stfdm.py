@@ -263,11 +263,12 @@ class BatchHandle(_Handle):
         self.hs = list(hs)   # the problem handles must outlive the plan
 
 
-def st_batch_create(hs, tol=0.0, max_sweeps=0, restart=0, no_graph=False, no_tune=False) -> BatchHandle:
+def st_batch_create(hs, tol=0.0, max_sweeps=0, restart=0, no_graph=False, no_tune=False, no_keep=False) -> BatchHandle:
     """Batched mixed-precision plan over FdmHandles of any mixture of sizes (see st_batch_create)."""
     n = len(hs)
     H = (ctypes.c_void_p * n)(*[h.ptr for h in hs])
-    o = _lib.st_batch_opts(float(tol), int(max_sweeps), int(restart), int(bool(no_graph)), int(bool(no_tune)))
+    o = _lib.st_batch_opts(float(tol), int(max_sweeps), int(restart), int(bool(no_graph)), int(bool(no_tune)),
+                           int(bool(no_keep)))
     out = ctypes.c_void_p()
     check(lib().st_batch_create(H, n, ctypes.byref(o), ctypes.byref(out)), "st_batch_create")
     return BatchHandle(out, hs)

@@ -136,6 +136,28 @@ def test_batch_graph_and_direct_launches_agree(dev, uneven):
         assert torch.equal(a, c)
 
 
+def test_batch_kept_factors(dev, uneven):
+    """With memory to spare every problem keeps its factors (later applications only stream them
+    through the grouped substitutions); without, every application refactorises.  Both meet the
+    oracle."""
+    from paper_2504_07269_gb300 import stfdm
+
+    hs, Fs, P0, refs = uneven
+    bk = stfdm.st_batch_create(hs, tol=1e-12)
+    bn = stfdm.st_batch_create(hs, tol=1e-12, no_keep=True)
+    sk, sn = stfdm.st_batch_stats_get(bk), stfdm.st_batch_stats_get(bn)
+    assert sk["kept_problems"] == len(hs) and sk["kept_factor_bytes"] > 0
+    assert sn["kept_problems"] == 0 and sn["kept_factor_bytes"] == 0
+    for b in (bk, bn):
+        outs, infos = stfdm.st_batch_solve(b, Fs, P0)
+        for o, ref, info in zip(outs, refs, infos):
+            assert rel(o.cpu().numpy(), ref) <= 1e-9, info
+    # a second solve on the kept plan refactorises for its new right-hand sides as well
+    outs2, _ = stfdm.st_batch_solve(bk, [2.0 * F for F in Fs], [None if p is None else 2.0 * p for p in P0])
+    for o, ref in zip(outs2, refs):
+        assert rel(o.cpu().numpy(), 2.0 * ref) <= 1e-9
+
+
 def test_batch_untuned_defaults_agree(dev, uneven):
     from paper_2504_07269_gb300 import stfdm
 
