@@ -147,8 +147,17 @@ def measured_peaks():
 
 
 def kernel_source_sha():
-    with open(os.path.join(ROOT, "paper_2504_07269_gb300", "csrc", "k_band.cu"), "rb") as fh:
-        return hashlib.sha256(fh.read()).hexdigest()[:16]
+    """Hash of the blocked-panel factor kernel's source (its section of k_band.cu and the shared
+    device header): the recorded DRAM traffic is used only while this is unchanged."""
+    csrc = os.path.join(ROOT, "paper_2504_07269_gb300", "csrc")
+    with open(os.path.join(csrc, "k_band.cu")) as fh:
+        text = fh.read()
+    start = text.index("// ------------------------------------------------------------------ complex64, blocked panel")
+    end = text.index("// ------------------------------------------------------------------ backward substitution by one CTA")
+    h = hashlib.sha256(text[start:end].encode())
+    with open(os.path.join(csrc, "device.cuh"), "rb") as fh:
+        h.update(fh.read())
+    return h.hexdigest()[:16]
 
 
 def profiled_traffic(config: str):

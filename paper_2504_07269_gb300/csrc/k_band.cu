@@ -286,20 +286,55 @@ __device__ __forceinline__ void band_factor_v4(const BandArgs<float>& a, const f
             }
         }
         __syncthreads();
-        // 2a. LDL^T of the 32 x 32 top block by the whole CTA: in step q, thread t updates
-        //     row r = t / 8 at columns q2 = q + 1 + t % 8 (+ 8, + 16, ...) <= r (unscaled form)
+        // 2a. LDL^T of the 32 x 32 top block by the whole CTA, two columns per step (one barrier per
+        //     step): thread t owns row r = t / 8 at columns q2 = q + 2 + t % 8 (+ 8, ...) <= r and applies
+        //     the eliminations of columns q and q + 1 together from the values before the step,
+        //       A''(r, q2) = A(r, q2) - A(r, q) A(q2, q) / d_q - A'(r, q+1) A'(q2, q+1) / d'_{q+1},
+        //       A'(i, q+1) = A(i, q+1) - A(i, q) A(q+1, q) / d_q,  d'_{q+1} = A'(q+1, q+1)
+        //     (unscaled form); column q + 1's new entries are stored after the step's barrier.  A last
+        //     odd column has no rows below it inside the block.
         {
             const int r = tid >> 3, g = tid & 7;
-            for (int q = 0; q < nbk; ++q) {
-                float2 d = P[q * WR + q];
-                if (bad_pivot<T>(d)) d = mk<T>(1e-30f, 0);
-                const float2 di = cinv<T>(d);
-                if (r > q && r < nbk) {
-                    const float2 x = P[q * WR + r];
-                    for (int q2 = q + 1 + g; q2 <= r; q2 += 8) cfms<T>(P[q2 * WR + r], x, cmul<T>(P[q * WR + q2], di));
+            float2 pend = mk<T>(0, 0);
+            int pend_col = -1;
+            for (int q = 0; q + 1 < nbk; q += 2) {
+                if (pend_col >= 0) {
+                    P[pend_col * WR + r] = pend;
+                    pend_col = -1;
+                }
+                float2 d0 = P[q * WR + q];
+                if (bad_pivot<T>(d0)) d0 = mk<T>(1e-30f, 0);
+                const float2 di0 = cinv<T>(d0);
+                const float2 f = cmul<T>(P[q * WR + (q + 1)], di0);      // A(q+1, q) / d_q
+                float2 d1 = P[(q + 1) * WR + (q + 1)];
+                cfms<T>(d1, P[q * WR + (q + 1)], f);
+                const float2 d1s = bad_pivot<T>(d1) ? mk<T>(1e-30f, 0) : d1;
+                const float2 di1 = cinv<T>(d1s);
+                if (r > q + 1 && r < nbk) {
+                    const float2 x0 = P[q * WR + r];
+                    float2 x1 = P[(q + 1) * WR + r];
+                    cfms<T>(x1, x0, f);
+                    for (int q2 = q + 2 + g; q2 <= r; q2 += 8) {
+                        const float2 c0 = P[q * WR + q2];
+                        float2 c1 = P[(q + 1) * WR + q2];
+                        cfms<T>(c1, c0, f);
+                        float2 v = P[q2 * WR + r];
+                        cfms<T>(v, x0, cmul<T>(c0, di0));
+                        cfms<T>(v, x1, cmul<T>(c1, di1));
+                        P[q2 * WR + r] = v;
+                    }
+                    if (g == 0) {
+                        pend = x1;
+                        pend_col = q + 1;
+                    }
+                } else if (r == q + 1 && g == 0) {
+                    pend = d1;
+                    pend_col = q + 1;
                 }
                 __syncthreads();
             }
+            if (pend_col >= 0) P[pend_col * WR + r] = pend;
+            __syncthreads();
         }
         // pivots, 1/d, scaled L11 and U[q'][q] = d_q' L(q, q')
         if (tid < nbk) {
