@@ -310,17 +310,9 @@ def run_ours(args):
     t_ms = reduce_max(t_ms, world, dev)
     value = world * pr.unknowns / (t_ms * 1e-3)
     sweeps = int(info.get("sweeps", 1)) if info else 1
-    # Our kernels per step (GMRES refinement, factors kept, tensor-core transforms), counted from the
-    # solver's control flow and matching the ncu launch list of one step:
-    #   A_x psi0 + set_scalars                                   2
-    #   per restart cycle: residual + reduction                  2
-    #   per non-final cycle: x += Z y                            1
-    #   per FDM32 application: 2 x (split + tcgen05 GEMM), factor (first) or forward substitution,
-    #     backward substitution, K z + reduction, 3 x (multi-dot + finalize), 2 multi-axpy, scale  17
-    #   psi0 added back                                          1
-    hist = [r for r in (info.get("residual_history") or []) if r >= 0] if info else []
-    cycles = max(1, len(hist))
-    launches_per_step = (17 * sweeps + 3 * cycles + 2) if args.precision == "mixed" else 6
+    # our kernels per step: the library counts the launches each solve issues (the ncu launch list of
+    # one step, profiles/launches_mixed_c2.md, agrees with it)
+    launches_per_step = int(info.get("kernel_launches", 0)) if info else 0
 
     # ---- end to end through the C ABI with host buffers (H2D of F and psi0, D2H of psi)
     Fh = F.cpu().pin_memory()

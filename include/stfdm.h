@@ -115,13 +115,14 @@ typedef struct {
     double min_neg_im_shift;     /* min_k (-Im s_k); >= 0 up to rounding */
     double setup_seconds;        /* host time of st_fdm_setup's FP64 decomposition */
     int tensor_cores;            /* 1 if the complex-FP32 time transforms ran on the tcgen05 tensor cores */
+    int kernel_launches;         /* kernels this call launched (st_fdm_solve, st_adjoint_solve; 0 in batched solves) */
 } st_solve_info;
 
 /* ------------------------------------------------------------------ status */
 const char* st_status_string(st_status s);
 const char* st_last_error_message(void);
 int st_abi_version(void);   /* returns STFDM_ABI_VERSION of the built library */
-#define STFDM_ABI_VERSION 3
+#define STFDM_ABI_VERSION 4
 
 /* ------------------------------------------------------------------ assembly (host) */
 /* Temporal matrices of eq. (matrix_t), Section 3.  p_t in {1, 2}: continuous piecewise

@@ -52,7 +52,7 @@ class st_solve_opts(ctypes.Structure):
 class st_solve_info(ctypes.Structure):
     _fields_ = [("sweeps", c_int), ("factors_kept", c_int), ("rel_residual", c_double),
                 ("residual_history", c_double * 16), ("kappa_x", c_double), ("min_neg_im_shift", c_double),
-                ("setup_seconds", c_double), ("tensor_cores", c_int)]
+                ("setup_seconds", c_double), ("tensor_cores", c_int), ("kernel_launches", c_int)]
 
 
 class st_batch_opts(ctypes.Structure):

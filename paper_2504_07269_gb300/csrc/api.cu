@@ -15,6 +15,10 @@
 
 namespace stfdm {
 
+thread_local long long t_launches = 0;
+void note_launches(int n) { t_launches += n; }
+long long launches_issued() { return t_launches; }
+
 // launchers implemented in the kernel files
 cudaError_t launch_stencil_A(const SpaceMats& sm, const void* in, bool in_c64, const double2* add, double sign,
                              double2* out, cudaStream_t st);
@@ -559,7 +563,8 @@ st_status solve_mixed_gmres(st_fdm* h, bool adjoint, const void* F, const void* 
             // w = K z_j (operator apply: no right-hand side)
             CUDA_TRY(launch_residual(h->sm, n_t, h->dt.Mb, Bband, bsign, nullptr, nullptr, h->dt.m, Zp(j), nullptr,
                                      w, parts, scal, st));
-            // two passes of classical Gram-Schmidt, then ||w||
+            // two passes of classical Gram-Schmidt, then ||w||: with a good preconditioner w = K z_j
+            // is close to v_j, so the first pass removes nearly all of it and the second is always needed
             CUDA_TRY(launch_multidot(P, j + 1, w, N, partial, hb, st));
             CUDA_TRY(launch_multiaxpy(P, j + 1, hb, -1.0, w, N, st));
             CUDA_TRY(launch_multidot(P, j + 1, w, N, partial, hb + MV, st));
@@ -821,8 +826,8 @@ extern "C" st_status st_fdm_get(const st_fdm* h, int* n_t, int* n_x, int* m, dou
 extern "C" void st_destroy_fdm(st_fdm* h) { free_handle(h); }
 
 // ==================================================================== solves
-extern "C" st_status st_fdm_solve(st_fdm* h, const void* F, const void* psi0, void* psi, const st_solve_opts* opts,
-                                  st_solve_info* info, void* stream) {
+static st_status fdm_solve_impl(st_fdm* h, const void* F, const void* psi0, void* psi, const st_solve_opts* opts,
+                                st_solve_info* info, void* stream) {
     if (!h) return fail(ST_ERR_ARG, "st_fdm_solve: NULL handle");
     if (!F || !psi) return fail(ST_ERR_ARG, "st_fdm_solve: NULL F or psi");
     if (F == psi) return fail(ST_ERR_ARG, "st_fdm_solve: psi must not alias F");
@@ -847,6 +852,14 @@ extern "C" st_status st_fdm_solve(st_fdm* h, const void* F, const void* psi0, vo
         return check_status_flag(h, st);
     }
     return ST_OK;
+}
+
+extern "C" st_status st_fdm_solve(st_fdm* h, const void* F, const void* psi0, void* psi, const st_solve_opts* opts,
+                                  st_solve_info* info, void* stream) {
+    const long long l0 = launches_issued();
+    const st_status s = fdm_solve_impl(h, F, psi0, psi, opts, info, stream);
+    if (info) info->kernel_launches = (int)(launches_issued() - l0);
+    return s;
 }
 
 extern "C" st_status st_residual(st_fdm* h, const void* F, const void* psi0, const void* psi, void* R,
@@ -875,8 +888,8 @@ extern "C" st_status st_residual(st_fdm* h, const void* F, const void* psi0, con
     return ST_OK;
 }
 
-extern "C" st_status st_adjoint_solve(st_fdm* h, const void* G, void* lambda, const st_solve_opts* opts,
-                                      st_solve_info* info, void* stream) {
+static st_status adjoint_solve_impl(st_fdm* h, const void* G, void* lambda, const st_solve_opts* opts,
+                                    st_solve_info* info, void* stream) {
     if (!h || !G || !lambda) return fail(ST_ERR_ARG, "st_adjoint_solve: NULL argument");
     if (G == lambda) return fail(ST_ERR_ARG, "st_adjoint_solve: lambda must not alias G");
     st_solve_opts o;
@@ -900,6 +913,14 @@ extern "C" st_status st_adjoint_solve(st_fdm* h, const void* G, void* lambda, co
         return check_status_flag(h, st);
     }
     return ST_OK;
+}
+
+extern "C" st_status st_adjoint_solve(st_fdm* h, const void* G, void* lambda, const st_solve_opts* opts,
+                                      st_solve_info* info, void* stream) {
+    const long long l0 = launches_issued();
+    const st_status s = adjoint_solve_impl(h, G, lambda, opts, info, stream);
+    if (info) info->kernel_launches = (int)(launches_issued() - l0);
+    return s;
 }
 
 extern "C" st_status st_adjoint_lift(st_fdm* h, const void* grad_psi, const void* grad_F, void* grad_psi0,

@@ -712,6 +712,7 @@ extern "C" st_status st_batch_solve(st_batch* b, const void* const* F, const voi
             inf.min_neg_im_shift = h->td.min_neg_im;
             inf.setup_seconds = h->setup_seconds;
             inf.tensor_cores = 0;
+            inf.kernel_launches = 0;
         }
         if (stopped[p] != 1 && bad < 0) bad = p;
     }

@@ -11,6 +11,11 @@
 
 namespace stfdm {
 
+// kernel launches issued by the calling host thread (counted by every launcher; a solve reports
+// the difference in st_solve_info::kernel_launches)
+void note_launches(int n);
+long long launches_issued();
+
 // ------------------------------------------------------------------ complex helpers
 template <typename T> struct cplx;
 template <> struct cplx<float> { using type = float2; };

@@ -678,6 +678,7 @@ static cudaError_t launch_factor_nb(const BandArgs<T>& a, int grid, cudaStream_t
     cudaError_t e = cudaFuncSetAttribute(k_band_factor_solve<T, NB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     k_band_factor_solve<T, NB><<<grid, 256, smem, st>>>(a);
+    note_launches(1);
     return cudaGetLastError();
 }
 
@@ -728,6 +729,7 @@ cudaError_t band_factor_solve_launch<float>(const BandArgs<float>& a, int nb, in
         cudaError_t e = cudaFuncSetAttribute(k_band_factor_v4, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
         k_band_factor_v4<<<grid, V4_THREADS, smem, st>>>(a);
+        note_launches(1);
         return cudaGetLastError();
     }
     if (nb == -16) return launch_factor_nb<float, 16>(a, grid, st);

@@ -105,6 +105,7 @@ cudaError_t launch_multidot(const double2* const* Vdev, int nv, const double2* w
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     k_multidot_finalize<<<1, KRY_MAXV, 0, st>>>(partial, KRY_BLOCKS, nv, out);
+    note_launches(2);
     return cudaGetLastError();
 }
 
@@ -112,16 +113,19 @@ cudaError_t launch_multiaxpy(const double2* const* Vdev, int nv, const double2* 
                              cudaStream_t st) {
     if (nv < 1 || nv > KRY_MAXV) return cudaErrorInvalidValue;
     k_multiaxpy<<<KRY_BLOCKS, 256, 0, st>>>(Vdev, nv, c, sign, y, n);
+    note_launches(1);
     return cudaGetLastError();
 }
 
 cudaError_t launch_scale(const double2* x, double alpha, double2* y, size_t n, cudaStream_t st) {
     k_scale<<<KRY_BLOCKS, 256, 0, st>>>(x, alpha, y, n);
+    note_launches(1);
     return cudaGetLastError();
 }
 
 cudaError_t launch_set_scalars(double* dst, double a, double b, cudaStream_t st) {
     k_set_scalars<<<1, 1, 0, st>>>(dst, a, b);
+    note_launches(1);
     return cudaGetLastError();
 }
 

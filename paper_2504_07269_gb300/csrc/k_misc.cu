@@ -236,6 +236,7 @@ cudaError_t launch_stencil_A(const SpaceMats& sm, const void* in, bool in_c64, c
     int grid = (sm.n_x + 255) / 256;
     if (in_c64) k_stencil_A<float><<<grid, 256, 0, st>>>(s, sm.n_x, (const float2*)in, add, sign, out);
     else k_stencil_A<double><<<grid, 256, 0, st>>>(s, sm.n_x, (const double2*)in, add, sign, out);
+    note_launches(1);
     return cudaGetLastError();
 }
 
@@ -265,6 +266,7 @@ cudaError_t launch_residual(const SpaceMats& sm, int n_t, const double* Mb, cons
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     k_reduce_finalize<<<1, 256, 0, st>>>(partials, (int)(grid.x * grid.y), scalars, (double)n_t * sm.n_x);
+    note_launches(2);
     return cudaGetLastError();
 }
 
@@ -273,6 +275,7 @@ cudaError_t launch_add_row(int n_t, int n_x, void* psi, const void* psi0, bool c
     int grid = (int)std::min<size_t>((total + 255) / 256, 152 * 32);
     if (c64) k_add_row<float><<<grid, 256, 0, st>>>(n_t, n_x, (float2*)psi, (const float2*)psi0);
     else k_add_row<double><<<grid, 256, 0, st>>>(n_t, n_x, (double2*)psi, (const double2*)psi0);
+    note_launches(1);
     return cudaGetLastError();
 }
 
@@ -280,12 +283,14 @@ cudaError_t launch_load_nodal(const SpaceMats& sm, int n_t, const double* Mb, co
                               const double2* f, double2* F, cudaStream_t st) {
     dim3 grid((sm.n_x + 255) / 256, n_t);
     k_load_nodal<<<grid, 256, 0, st>>>(n_t, sm.n_x, make_stencil(sm), Mb, Mfull0, f, F);
+    note_launches(1);
     return cudaGetLastError();
 }
 
 cudaError_t launch_colsums(int n_t, int n_x, const double2* U1, const double2* U2, const double* w, double2* out1,
                            double2* out2, cudaStream_t st) {
     k_colsums<<<(n_x + 255) / 256, 256, 0, st>>>(n_t, n_x, U1, U2, w, out1, out2);
+    note_launches(1);
     return cudaGetLastError();
 }
 

@@ -349,6 +349,7 @@ static cudaError_t launch_src(const Src& src, int count, int sb, int* status, bo
     const int blocks = std::max(1, std::min(count, occ * sms));
     if (fwd) k_subst_fwd<T, R, G, Src><<<blocks, 64, smem, st>>>(src, sb, status);
     else k_subst_bwd<T, R, G, Src><<<blocks, 64, smem, st>>>(src, sb, status);
+    note_launches(1);
     return cudaGetLastError();
 }
 

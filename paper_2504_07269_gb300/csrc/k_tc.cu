@@ -385,6 +385,7 @@ cudaError_t tc_split_launch(const void* in, bool in_c128, int K, int N, int K_pa
     else
         tc::k_tc_split<float><<<grid, 256, 0, st>>>(reinterpret_cast<const float2*>(in), K, N, K_pad, N2_pad, scale,
                                                     conj, bt);
+    note_launches(1);
     return cudaGetLastError();
 }
 
@@ -414,6 +415,7 @@ cudaError_t tc_gemm_launch(const CUtensorMap& mapA, const CUtensorMap& mapB, int
     e.err = err;
     dim3 grid(M_pad / tc::BM, N2_pad / tc::BN);
     tc::k_xform_tc<<<grid, tc::THREADS, tc::SMEM_BYTES, st>>>(mapA, mapB, M_pad, N2_pad, K_pad, e);
+    note_launches(1);
     return cudaGetLastError();
 }
 

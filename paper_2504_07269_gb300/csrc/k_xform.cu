@@ -107,6 +107,7 @@ template <typename TA, typename TB, typename TC, typename TACC>
 cudaError_t xform_simt_launch(const XformArgs<TA, TB, TC>& a, cudaStream_t st) {
     dim3 grid((a.N + XBN - 1) / XBN, (a.M + XBM - 1) / XBM);
     k_xform_simt<TA, TB, TC, TACC><<<grid, 256, 0, st>>>(a);
+    note_launches(1);
     return cudaGetLastError();
 }
 

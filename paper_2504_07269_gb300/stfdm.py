@@ -111,7 +111,7 @@ def _info_dict(info: _lib.st_solve_info):
     return dict(sweeps=info.sweeps, factors_kept=info.factors_kept, rel_residual=info.rel_residual,
                 residual_history=[v for v in info.residual_history if v >= 0], kappa_x=info.kappa_x,
                 min_neg_im_shift=info.min_neg_im_shift, setup_seconds=info.setup_seconds,
-                tensor_cores=info.tensor_cores)
+                tensor_cores=info.tensor_cores, kernel_launches=info.kernel_launches)
 
 
 # ------------------------------------------------------------------ assembly / setup

@@ -67,6 +67,7 @@ def test_c1_manufactured(dev):
     assert rel(psi.cpu().numpy(), ref) <= 1e-9, info
     assert info["rel_residual"] <= 1e-12 and info["sweeps"] >= 1
     assert info["tensor_cores"] == 1   # the FP32 transforms ran on tcgen05
+    assert info["kernel_launches"] >= 10 * info["sweeps"]   # counted by the library's launchers
     psi32, _ = stfdm.st_fdm_solve(h, Fd.to(torch.complex64), p0.to(torch.complex64), precision="fp32")
     e32 = rel(psi32.cpu().numpy(), ref)
     print(f"c1 fp32 rel. error {e32:.2e}")
