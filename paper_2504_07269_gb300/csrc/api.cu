@@ -23,7 +23,7 @@ long long launches_issued() { return t_launches; }
 cudaError_t launch_stencil_A(const SpaceMats& sm, const void* in, bool in_c64, const double2* add, double sign,
                              double2* out, cudaStream_t st);
 int residual_num_partials(int n_t, int n_x);
-cudaError_t launch_residual(const SpaceMats& sm, int n_t, const double* Mb, const double* Bb, double bsign,
+cudaError_t launch_residual(const SpaceMats& sm, int n_t, int time_band, const double* Mb, const double* Bb, double bsign,
                             const double2* F, const double2* apsi0, const double* m_t, const double2* U,
                             const double2* psi0, double2* R, double* partials, double* scalars, cudaStream_t st);
 cudaError_t launch_add_row(int n_t, int n_x, void* psi, const void* psi0, bool c64, cudaStream_t st);
@@ -282,6 +282,9 @@ st_status band_run(st_fdm* h, C<T>* G, int mode, cudaStream_t st) {
     return ST_OK;
 }
 
+// nonzero diagonals of the temporal band matrices: 3 for P1 time, 5 for P2
+int time_band(const st_fdm* h) { return h->tm.p == 1 ? 3 : 5; }
+
 st_status check_status_flag(st_fdm* h, cudaStream_t st) {
     int flag[2] = {0, 0};
     CUDA_TRY(cudaMemcpyAsync(flag, h->ws_status, 2 * sizeof(int), cudaMemcpyDeviceToHost, st));
@@ -378,7 +381,7 @@ st_status solve_mixed(st_fdm* h, bool adjoint, const void* F, const void* psi0, 
     double rel = -1;
     bool converged = false;
     for (int sw = 0; sw <= nsweeps; ++sw) {
-        CUDA_TRY(launch_residual(h->sm, n_t, h->dt.Mb, Bband, bsign, reinterpret_cast<const double2*>(F), apsi0,
+        CUDA_TRY(launch_residual(h->sm, n_t, time_band(h), h->dt.Mb, Bband, bsign, reinterpret_cast<const double2*>(F), apsi0,
                                  h->dt.m, sw == 0 ? nullptr : reinterpret_cast<const double2*>(psi), nullptr, R, parts,
                                  scal, st));
         if (!fixed || sw == nsweeps) {
@@ -537,7 +540,7 @@ st_status solve_mixed_gmres(st_fdm* h, bool adjoint, const void* F, const void* 
     std::vector<double> cs(m);
     std::vector<double2> hh(3 * MV);
     while (true) {
-        CUDA_TRY(launch_residual(h->sm, n_t, h->dt.Mb, Bband, bsign, reinterpret_cast<const double2*>(F), apsi0,
+        CUDA_TRY(launch_residual(h->sm, n_t, time_band(h), h->dt.Mb, Bband, bsign, reinterpret_cast<const double2*>(F), apsi0,
                                  h->dt.m, x_zero ? nullptr : x, nullptr, w, parts, scal, st));
         double hs[2];
         CUDA_TRY(cudaMemcpyAsync(hs, scal, 2 * sizeof(double), cudaMemcpyDeviceToHost, st));
@@ -561,7 +564,7 @@ st_status solve_mixed_gmres(st_fdm* h, bool adjoint, const void* F, const void* 
             if (s != ST_OK) return s;
             ++its;
             // w = K z_j (operator apply: no right-hand side)
-            CUDA_TRY(launch_residual(h->sm, n_t, h->dt.Mb, Bband, bsign, nullptr, nullptr, h->dt.m, Zp(j), nullptr,
+            CUDA_TRY(launch_residual(h->sm, n_t, time_band(h), h->dt.Mb, Bband, bsign, nullptr, nullptr, h->dt.m, Zp(j), nullptr,
                                      w, parts, scal, st));
             // two passes of classical Gram-Schmidt, then ||w||: with a good preconditioner w = K z_j
             // is close to v_j, so the first pass removes nearly all of it and the second is always needed
@@ -876,7 +879,7 @@ extern "C" st_status st_residual(st_fdm* h, const void* F, const void* psi0, con
     }
     double* scal = h->ws_red + 4;
     double* parts = h->ws_red + 8;
-    CUDA_TRY(launch_residual(h->sm, h->tm.n_t, h->dt.Mb, h->dt.Bb, 1.0, reinterpret_cast<const double2*>(F), apsi0,
+    CUDA_TRY(launch_residual(h->sm, h->tm.n_t, time_band(h), h->dt.Mb, h->dt.Bb, 1.0, reinterpret_cast<const double2*>(F), apsi0,
                              h->dt.m, reinterpret_cast<const double2*>(psi), reinterpret_cast<const double2*>(psi0),
                              reinterpret_cast<double2*>(R), parts, scal, st));
     if (rel_norm) {

@@ -404,6 +404,7 @@ extern "C" st_status st_batch_create(st_fdm* const* hs, int count, const st_batc
         pr.n_t = n_t;
         pr.n_x = n_x;
         pr.m = h->sm.m;
+        pr.tband = h->tm.p == 1 ? 3 : 5;
         pr.Mc = h->sm.Mc; pr.Mw = h->sm.Mw; pr.Ms = h->sm.Ms; pr.Md = h->sm.Md;
         pr.Ac = h->sm.Ac; pr.Aw = h->sm.Aw; pr.As = h->sm.As; pr.Ad = h->sm.Ad;
         pr.Mb = h->dt.Mb;

@@ -135,7 +135,7 @@ cudaError_t subst_batch_launch(const BatchBand* probs, const int2* items, int n_
 
 // batched solve: per-problem descriptor and per-problem GMRES state (device arrays)
 struct BatchProb {
-    int n_t, n_x, m, pad;
+    int n_t, n_x, m, tband;   // tband: nonzero temporal band diagonals (3 for P1 time, 5 for P2)
     double Mc, Mw, Ms, Md, Ac, Aw, As, Ad;
     const double* Mb;       // n_t x 5 band of M_t
     const double* Bb;       // n_t x 5 band of B_t

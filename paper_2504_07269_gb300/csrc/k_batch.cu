@@ -110,8 +110,10 @@ __global__ void __launch_bounds__(KB_THREADS) kb_residual(const BatchProb* probs
             }
             row(l + 2, Pv[4], Qv[4]);
             double2 kv = make_double2(0, 0);
+            const int dlo = 2 - pr.tband / 2, dhi = 2 + pr.tband / 2;
 #pragma unroll
             for (int d = 0; d < 5; ++d) {
+                if (d < dlo || d > dhi) continue;
                 const double bc = pr.Bb[l * 5 + d], mc = pr.Mb[l * 5 + d];
                 kv.x += -bc * Pv[d].y + mc * Qv[d].x;
                 kv.y += bc * Pv[d].x + mc * Qv[d].y;

@@ -81,6 +81,8 @@ __device__ __forceinline__ double block_sum(double v, double* red) {
     return t;
 }
 
+// TB: nonzero diagonals of the temporal bands (3 for P1 time, 5 for P2)
+template <int TB>
 __global__ void __launch_bounds__(256) k_residual(ResArgs a) {
     __shared__ double red[32];
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
@@ -120,7 +122,7 @@ __global__ void __launch_bounds__(256) k_residual(ResArgs a) {
             double2 ft = make_double2(f.x - ml * ap.x, f.y - ml * ap.y);
             double2 kv = make_double2(0, 0);
 #pragma unroll
-            for (int d = 0; d < 5; ++d) {
+            for (int d = 2 - TB / 2; d <= 2 + TB / 2; ++d) {
                 const double bc = a.bsign * a.Bb[l * 5 + d];
                 const double mc = a.Mb[l * 5 + d];
                 // i * bc * P + mc * Q
@@ -244,7 +246,7 @@ int residual_num_partials(int n_t, int n_x) {
     return ((n_x + 255) / 256) * ((n_t + RES_LT - 1) / RES_LT);
 }
 
-cudaError_t launch_residual(const SpaceMats& sm, int n_t, const double* Mb, const double* Bb, double bsign,
+cudaError_t launch_residual(const SpaceMats& sm, int n_t, int time_band, const double* Mb, const double* Bb, double bsign,
                             const double2* F, const double2* apsi0, const double* m_t, const double2* U,
                             const double2* psi0, double2* R, double* partials, double* scalars, cudaStream_t st) {
     ResArgs a;
@@ -262,7 +264,8 @@ cudaError_t launch_residual(const SpaceMats& sm, int n_t, const double* Mb, cons
     a.R = R;
     a.partials = partials;
     dim3 grid((sm.n_x + 255) / 256, (n_t + RES_LT - 1) / RES_LT);
-    k_residual<<<grid, 256, 0, st>>>(a);
+    if (time_band == 3) k_residual<3><<<grid, 256, 0, st>>>(a);
+    else k_residual<5><<<grid, 256, 0, st>>>(a);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     k_reduce_finalize<<<1, 256, 0, st>>>(partials, (int)(grid.x * grid.y), scalars, (double)n_t * sm.n_x);
