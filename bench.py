@@ -384,13 +384,17 @@ def run_ours(args):
         times.append(e0.elapsed_time(e1) * 1e-3)
     tk = statistics.median(times)
     b = pr.n - 1 + 1
-    flops = 8.0 * pr.n_t * pr.n_x * b * b / 2.0      # complex MAC = 8 real flops; n_x b^2/2 per system
+    # complex MAC = 8 real flops; per system n_x b^2/2 for the factorisation, plus n_x b for each of
+    # the two substitutions when the FP32 kernel fuses them (the FP64 kernel leaves the backward one
+    # to the substitution kernel, whose time is in tk as well)
+    flops = 8.0 * pr.n_t * pr.n_x * (b * b / 2.0 + 2.0 * b)
     props = torch.cuda.get_device_properties(dev)
     max_mhz = (clocks or {}).get("sm_max_mhz") or (measured_peaks() or {}).get("sm_max_mhz", 2070.0)
     lanes = 128 if kprec == "fp32" else 2             # FP32 / FP64 FMA lanes per SM per clock
     peak = props.multi_processor_count * lanes * 2 * max_mhz * 1e6 / 1e12
     achieved = flops / tk / 1e12
-    roof = {"bound": "alu", "kernel": "k_band_factor_v4 (complex64)" if kprec == "fp32" else "k_band_factor_solve<double,32>",
+    roof = {"bound": "alu", "kernel": "k_band_factor_v4 (complex64, factor + both substitutions)" if kprec == "fp32"
+            else "k_band_factor_solve<double,32> + k_subst_bwd<double>",
             "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
             "traffic": profiled_traffic(args.config), "launch_ms": tk * 1e3,
             "peak_basis": f"{props.multi_processor_count} SMs x {lanes} {kprec.upper()} FMA lanes x 2 x {max_mhz:.0f} MHz "
@@ -530,7 +534,8 @@ def run_batch(args):
         torch.cuda.synchronize()
         times.append(e0.elapsed_time(e1) * 1e-3)
     tk = statistics.median(times)
-    flops = sum(8.0 * pr.n_t * pr.n_x * pr.n * pr.n / 2.0 for pr in probs)   # b = n per problem
+    # factorisation n_x b^2/2 plus both substitutions 2 n_x b complex MAC per system; b = n per problem
+    flops = sum(8.0 * pr.n_t * pr.n_x * (pr.n * pr.n / 2.0 + 2.0 * pr.n) for pr in probs)
     # the plan's workspace (kept factors included) is released before the FP64 reference solves
     stfdm.st_destroy_batch(b)
     torch.cuda.synchronize()
