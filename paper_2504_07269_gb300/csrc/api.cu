@@ -241,7 +241,6 @@ st_status band_run(st_fdm* h, C<T>* G, int mode, cudaStream_t st) {
     a.shifts = shifts_of<T>(h);
     a.rhs = G;
     a.status = h->ws_status;
-    a.fuse_bwd = 0;
     const int nbw = nb == 64 ? 32 : (nb < 0 ? -nb : nb);   // panel width of the selected kernel
     const size_t WR = (size_t)b + nbw;
     if (mode == 2) {
@@ -269,16 +268,12 @@ st_status band_run(st_fdm* h, C<T>* G, int mode, cudaStream_t st) {
     a.L = reinterpret_cast<C<T>*>(h->ws_L);
     a.D = reinterpret_cast<C<T>*>(h->ws_D);
     a.keep = (mode == 1) ? 1 : 0;
-    // the blocked-panel kernel solves each system's backward substitution itself, right after its
-    // factorisation (CTAs that finish early fill the launch's tail with it); the others leave it to
-    // the substitution kernel
-    a.fuse_bwd = (nb == 64) ? 1 : 0;
     for (int k0 = 0; k0 < n_t; k0 += chunk) {
         const int cnt = std::min(chunk, n_t - k0);
         a.k0 = k0;
         a.n_sys = cnt;
         CUDA_TRY(band_factor_solve_launch<T>(a, nb, std::min(grid, cnt), st));
-        if (!a.fuse_bwd) CUDA_TRY(subst_launch<T>(a, k0, cnt, false, st));
+        CUDA_TRY(subst_launch<T>(a, k0, cnt, false, st));
     }
     if (mode == 1) {
         h->factors_valid = 1;

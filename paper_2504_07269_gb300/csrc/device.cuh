@@ -98,7 +98,6 @@ struct BandArgs {
     C<T>* L;              // factor columns: L[j*b + o - 1] = L(j + o, j), o = 1..b
     C<T>* D;              // pivots
     int keep;             // 1: factors stored per system k, 0: per system of this launch (slot k - k0)
-    int fuse_bwd;         // 1: the complex64 blocked-panel kernel also solves L^T w = y per system
     int* status;          // status[0] set to 1 on a zero / non-finite pivot
 };
 // panel width code: the panel width (32/16/8), negative for the unstaged complex64 kernel, 0 = too wide

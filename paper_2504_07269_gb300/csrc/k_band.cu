@@ -496,24 +496,15 @@ size_t band_batch_smem(int b_max) {
     return f > bwd ? f : bwd;
 }
 
-__device__ __forceinline__ void band_bwd_cta(int n, int b, const float2* __restrict__ L, float2* z, char* smem);
-
-// One CTA per system (grid-stride): factorisation with the fused forward substitution, then, with
-// a.fuse_bwd, the backward substitution by the same CTA from the columns it has just written.
 __global__ void __launch_bounds__(V4_THREADS, 2) k_band_factor_v4(BandArgs<float> a) {
     extern __shared__ __align__(16) char smem[];
     const int WR = a.b + V4_NB, WB = a.b + 1;
     for (int ks = blockIdx.x; ks < a.n_sys; ks += gridDim.x) {
         const int k = a.k0 + ks;
         const size_t slot = a.keep ? (size_t)k : (size_t)ks;
-        float2* z = a.rhs + (size_t)k * a.n;
-        float2* Lk = a.L + slot * (size_t)a.n * a.b;
-        band_factor_v4(a, a.shifts[k], z, Lk, a.D + slot * (size_t)a.n, a.win + (size_t)blockIdx.x * WR * WB, smem);
+        band_factor_v4(a, a.shifts[k], a.rhs + (size_t)k * a.n, a.L + slot * (size_t)a.n * a.b, a.D + slot * (size_t)a.n,
+                       a.win + (size_t)blockIdx.x * WR * WB, smem);
         __syncthreads();
-        if (a.fuse_bwd) {
-            band_bwd_cta(a.n, a.b, Lk, z, smem);
-            __syncthreads();
-        }
     }
 }
 
@@ -734,7 +725,7 @@ cudaError_t band_factor_solve_launch<double>(const BandArgs<double>& a, int nb, 
 template <>
 cudaError_t band_factor_solve_launch<float>(const BandArgs<float>& a, int nb, int grid, cudaStream_t st) {
     if (nb == 64) {
-        size_t smem = a.fuse_bwd ? band_batch_smem(a.b) : band_factor_v4_smem(a.b);
+        size_t smem = band_factor_v4_smem(a.b);
         cudaError_t e = cudaFuncSetAttribute(k_band_factor_v4, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
         k_band_factor_v4<<<grid, V4_THREADS, smem, st>>>(a);
