@@ -147,22 +147,25 @@ def measured_peaks():
 
 
 def kernel_source_sha():
-    """Hash of the blocked-panel factor kernel's source (its section of k_band.cu and the shared
-    device header): the recorded DRAM traffic is used only while this is unchanged."""
+    """Hash of the source of the kernels the FP32 spatial solve runs (the blocked-panel factor
+    kernel's section of k_band.cu, the substitution kernels and the shared device header): the
+    recorded DRAM traffic is used only while this is unchanged."""
     csrc = os.path.join(ROOT, "paper_2504_07269_gb300", "csrc")
     with open(os.path.join(csrc, "k_band.cu")) as fh:
         text = fh.read()
     start = text.index("// ------------------------------------------------------------------ complex64, blocked panel")
     end = text.index("// ------------------------------------------------------------------ backward substitution by one CTA")
     h = hashlib.sha256(text[start:end].encode())
-    with open(os.path.join(csrc, "device.cuh"), "rb") as fh:
-        h.update(fh.read())
+    for name in ("k_subst.cu", "async.cuh", "device.cuh"):
+        with open(os.path.join(csrc, name), "rb") as fh:
+            h.update(fh.read())
     return h.hexdigest()[:16]
 
 
 def profiled_traffic(config: str):
-    """DRAM bytes per launch of the band factorisation from the committed ncu summary,
-    or None if the kernel source changed since the capture."""
+    """DRAM bytes of one FP32 spatial solve (factorisation with the fused forward substitution,
+    then the backward substitution) from the committed ncu summary, or None if the kernels' source
+    changed since the capture."""
     p = os.path.join(ROOT, "profiles", "traffic.json")
     if not os.path.exists(p):
         return None

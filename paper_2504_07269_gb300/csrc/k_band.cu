@@ -509,14 +509,8 @@ __global__ void __launch_bounds__(V4_THREADS, 2) k_band_factor_v4(BandArgs<float
 }
 
 // ------------------------------------------------------------------ backward substitution by one CTA
-// L^T w = y for one system whose factor columns L (L[j*b + o - 1] = L(j + o, j)) this CTA has just
-// written; z holds y on entry and w on exit.  Rows are solved in blocks of 32 from the bottom:
-//   A. every warp forms, for 4 of the block's columns j, the contribution of the already solved
-//      rows below the block, sum_{j + o >= j1} L(j + o, j) w_{j+o} (lanes across the band);
-//   B. warp 0 solves the 32 x 32 unit upper triangle of the block by shuffles, lane = row, with
-//      the block's in-triangle entries of L staged in shared memory during A.
-// The solved w of the last b + 32 rows stay in a shared-memory ring.
-__device__ __forceinline__ void band_bwd_cta(int n, int b, const float2* __restrict__ L, float2* z, char* smem) {
+// The same for bands wider than 256 (entries loaded when they are used).
+__device__ __forceinline__ void band_bwd_cta_wide(int n, int b, const float2* __restrict__ L, float2* z, char* smem) {
     using T = float;
     const int RB = b + 32;
     float2* ring = reinterpret_cast<float2*>(smem);   // [RB]: w of row r at r % RB
@@ -552,6 +546,98 @@ __device__ __forceinline__ void band_bwd_cta(int n, int b, const float2* __restr
             if (lane == 0) tcon[c] = acc;
         }
         __syncthreads();
+        if (warp == 0) {
+            const int j = j0 + lane;
+            float2 acc = (j < j1) ? csub<T>(z[j], tcon[lane]) : mk<T>(0, 0);
+#pragma unroll
+            for (int r = 31; r > 0; --r) {
+                const float2 wr = mk<T>(__shfl_sync(0xffffffffu, acc.x, r), __shfl_sync(0xffffffffu, acc.y, r));
+                if (lane < r) cfms<T>(acc, Ls[r * 33 + lane], wr);
+            }
+            if (j < j1) {
+                ring[j % RB] = acc;
+                z[j] = acc;
+            }
+        }
+        __syncthreads();
+    }
+}
+
+// L^T w = y for one system whose factor columns L (L[j*b + o - 1] = L(j + o, j)) this CTA has just
+// written; z holds y on entry and w on exit.  Rows are solved in blocks of 32 from the bottom:
+//   A. every warp forms, for 4 of the block's columns j, the contribution of the already solved
+//      rows below the block, sum_{j + o >= j1} L(j + o, j) w_{j+o} (lanes across the band);
+//   B. warp 0 solves the 32 x 32 unit upper triangle of the block by shuffles, lane = row, with
+//      the block's in-triangle entries of L staged in shared memory.
+// The solved w of the last b + 32 rows stay in a shared-memory ring.  For b <= 256 the entries of
+// L that block j0 - 32 needs (they do not depend on w) are loaded into registers while warp 0
+// solves block j0, so the loads' latency is off the block-to-block chain.
+__device__ __forceinline__ void band_bwd_cta(int n, int b, const float2* __restrict__ L, float2* z, char* smem) {
+    using T = float;
+    if (b > 256) {
+        band_bwd_cta_wide(n, b, L, z, smem);
+        return;
+    }
+    constexpr int NO = 8;   // band offsets per lane and column (b <= 8 x 32)
+    const int RB = b + 32;
+    float2* ring = reinterpret_cast<float2*>(smem);   // [RB]: w of row r at r % RB
+    float2* tcon = ring + RB;                          // [32]: contributions from below the block
+    float2* Ls = tcon + 32;                            // [32][33]: Ls[r][q] = L(j0 + r, j0 + q), q < r
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    float2 lv[4][NO];   // lv[cc][t] = L(j1 + lane + 32 t, j) for the warp's column j = j0 + 4 warp + cc
+    float2 lt[4];       // the thread's 4 entries of the block's strictly lower triangle
+    auto load = [&](int j0) {
+        const int j1 = min(j0 + 32, n);
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+            const int idx = tid + 256 * e, r = idx >> 5, q = idx & 31, o = r - q;
+            lt[e] = (o >= 1 && o <= b && j0 + r < j1) ? L[(size_t)(j0 + q) * b + (o - 1)] : mk<T>(0, 0);
+        }
+#pragma unroll
+        for (int cc = 0; cc < 4; ++cc) {
+            const int j = j0 + warp * 4 + cc;
+            const int ohi = (j < j1) ? min(b, n - 1 - j) : -1;
+            const float2* Lj = L + (size_t)j * b - 1;
+#pragma unroll
+            for (int t = 0; t < NO; ++t) {
+                const int o = j1 - j + lane + 32 * t;
+                lv[cc][t] = (o <= ohi) ? Lj[o] : mk<T>(0, 0);
+            }
+        }
+    };
+    int j0 = ((n - 1) / 32) * 32;
+    load(j0);
+    for (; j0 >= 0; j0 -= 32) {
+        const int j1 = min(j0 + 32, n);
+        const int j1m = j1 % RB;
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+            const int idx = tid + 256 * e;
+            Ls[(idx >> 5) * 33 + (idx & 31)] = lt[e];
+        }
+#pragma unroll
+        for (int cc = 0; cc < 4; ++cc) {
+            const int c = warp * 4 + cc, j = j0 + c;
+            const int ohi = (j < j1) ? min(b, n - 1 - j) : -1;
+            float2 acc = mk<T>(0, 0);
+#pragma unroll
+            for (int t = 0; t < NO; ++t) {
+                const int o = j1 - j + lane + 32 * t;
+                if (o <= ohi) {
+                    int r = j1m + lane + 32 * t;   // (j + o) % RB: j + o - j1 < b < RB
+                    if (r >= RB) r -= RB;
+                    cfma<T>(acc, lv[cc][t], ring[r]);
+                }
+            }
+#pragma unroll
+            for (int off = 16; off > 0; off >>= 1) {
+                acc.x += __shfl_xor_sync(0xffffffffu, acc.x, off);
+                acc.y += __shfl_xor_sync(0xffffffffu, acc.y, off);
+            }
+            if (lane == 0) tcon[c] = acc;
+        }
+        __syncthreads();
+        if (j0 >= 32) load(j0 - 32);
         if (warp == 0) {
             const int j = j0 + lane;
             float2 acc = (j < j1) ? csub<T>(z[j], tcon[lane]) : mk<T>(0, 0);
