@@ -8,7 +8,8 @@ of f = i d_t psi - Laplace psi (built on the device by st_load_nodal); psi0 = ps
 
 One step = one full st_fdm_solve (lifting, forward transform, banded LDL^T factor and
 solve of all 512 spatial systems, back transform, FP64 residual, refinement sweeps until
-||R||/||F~|| <= 1e-12).  The inputs (533 MB) exceed the 129 MB L2, so no flush is needed.
+||R||/||F~|| <= 1e-11, see SINGLE_TOL).  The inputs (533 MB) exceed the 129 MB L2, so no
+flush is needed.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
@@ -244,10 +245,17 @@ def run_reference(args):
     return 0
 
 
+# Relative residual target of the single-problem mixed solve.  On the 256^2/512 workload the error
+# against the FP64 FDM is about 6x the final residual, so 1e-11 keeps it two orders below the
+# metric's 1e-9 bar (the line prints it); 1e-12 sits at the FP64 residual floor (the GMRES estimate
+# reaches 5e-13 while the true residual is 1.2e-12) and costs a second restart cycle.
+SINGLE_TOL = 1e-11
+
+
 def _config(pr, args):
     return {"workload": f"{pr.n}x{pr.n} squares P1 space ({pr.n_x} nodes), P{pr.p_t} time {len(pr.t_nodes) - 1} "
                         f"uniform elements (n_t={pr.n_t}), T={pr.t_nodes[-1]:g}; {pr.unknowns} unknowns",
-            "name": pr.name, "precision": args.precision, "tol": 1e-12, "n_x": pr.n_x, "n_t": pr.n_t,
+            "name": pr.name, "precision": args.precision, "tol": SINGLE_TOL, "n_x": pr.n_x, "n_t": pr.n_t,
             "unknowns": pr.unknowns, "l2_flush": "inputs (533 MB c128 load) larger than the 129 MB L2",
             "parallelism": "replicas" if args.gpus > 1 else "single GPU"}
 
@@ -284,7 +292,7 @@ def run_ours(args):
             print(json.dumps({"profile_xform": args.config, "norm": float(torch.linalg.vector_norm(G32))}))
         return 0
     if args.profile_step:
-        _, info = stfdm.st_fdm_solve(h, F, p0, psi=psi, precision=args.precision)
+        _, info = stfdm.st_fdm_solve(h, F, p0, psi=psi, precision=args.precision, tol=SINGLE_TOL)
         torch.cuda.synchronize()
         if rank == 0:
             print(json.dumps({"profile_step": args.config, "precision": args.precision, "info": info}))
@@ -292,7 +300,7 @@ def run_ours(args):
 
     def step():
         nonlocal info
-        _, info = stfdm.st_fdm_solve(h, F, p0, psi=psi, precision=args.precision)
+        _, info = stfdm.st_fdm_solve(h, F, p0, psi=psi, precision=args.precision, tol=SINGLE_TOL)
 
     for _ in range(args.warmup):
         step()
@@ -327,7 +335,7 @@ def run_ours(args):
     def e2e_step():
         Fd.copy_(Fh, non_blocking=True)
         p0d.copy_(p0h, non_blocking=True)
-        stfdm.st_fdm_solve(h, Fd, p0d, psi=psi, precision=args.precision, want_info=False)
+        stfdm.st_fdm_solve(h, Fd, p0d, psi=psi, precision=args.precision, tol=SINGLE_TOL, want_info=False)
         psih.copy_(psi, non_blocking=True)
 
     e2e_step()
@@ -356,7 +364,7 @@ def run_ours(args):
         e1.record()
         torch.cuda.synchronize()
         fp64_value = pr.unknowns / (e0.elapsed_time(e1) * 1e-3)
-        stfdm.st_fdm_solve(h, F, p0, psi=psi, precision=args.precision, want_info=False)
+        stfdm.st_fdm_solve(h, F, p0, psi=psi, precision=args.precision, tol=SINGLE_TOL, want_info=False)
         err = float(torch.linalg.vector_norm(psi.to(torch.complex128) - ref) / torch.linalg.vector_norm(ref))
         # the plain complex-FP32 FDM on the same inputs (3xTF32 tensor-core transforms, FP32 solves)
         F32, p032 = F.to(torch.complex64), p0.to(torch.complex64)
