@@ -108,7 +108,8 @@ typedef struct {
 
 typedef struct {
     int sweeps;                  /* FDM sweeps run (1 for ST_FP64 / ST_FP32) */
-    int factors_kept;            /* 1 if the LDL^T factors were reused across sweeps */
+    int factors_kept;            /* 1 if the LDL^T factors were reused across sweeps, 2 if only
+                                    those of the leading systems that fit in memory (GMRES) */
     double rel_residual;         /* final ||F~ - K psi_hat|| / ||F~|| (computed for ST_MIXED; -1 otherwise) */
     double residual_history[16]; /* rel. residual before each sweep (ST_MIXED), then the final one */
     double kappa_x;              /* kappa_2(X_t) */

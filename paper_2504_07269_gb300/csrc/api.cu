@@ -77,6 +77,17 @@ st_status grow(void*& p, size_t& have, size_t need, const char* what) {
     return s;
 }
 
+// exactly `need` bytes (reallocated unless the size matches)
+st_status resize(void*& p, size_t& have, size_t need, const char* what) {
+    if (need == have && p) return ST_OK;
+    if (p) cudaFree(p);
+    p = nullptr;
+    have = 0;
+    st_status s = dev_alloc(&p, need, what);
+    if (s == ST_OK) have = need;
+    return s;
+}
+
 template <typename T>
 st_status upload(T** dst, const void* src, size_t bytes, const char* what) {
     st_status s = dev_alloc((void**)dst, bytes, what);
@@ -122,6 +133,8 @@ void free_handle(st_fdm* h) {
     cudaFree(h->ws_win);
     cudaFree(h->ws_L);
     cudaFree(h->ws_D);
+    cudaFree(h->ws_Lt);
+    cudaFree(h->ws_Dt);
     cudaFree(h->ws_vec);
     cudaFree(h->ws_red);
     cudaFree(h->ws_status);
@@ -211,6 +224,32 @@ const double2* shifts_of<double>(const st_fdm* h) { return h->s64; }
 template <>
 const float2* shifts_of<float>(const st_fdm* h) { return h->s32; }
 
+// Partial keep when not all complex64 factors fit: the number K of leading systems whose factors
+// stay in memory, as many as fit in 90% of the memory left after one wave of transient factors
+// (one system per resident CTA), rounded down so that the n_t - K systems refactorised at every
+// application fill whole waves (a wave costs the same whether full or not).  0 if none fit.
+int partial_keep_count(st_fdm* h) {
+    const int n_t = h->tm.n_t, n = h->sm.n_x, b = h->sm.m + 1;
+    const int nb = band_pick_nb<float>(b, h->smem_optin);
+    if (nb == 0) return 0;
+    int occ = band_occupancy<float>(nb, b);
+    if (occ < 1) occ = 1;
+    const int grid = std::max(1, std::min(n_t, occ * h->sm_count));
+    const size_t per = (size_t)n * (size_t)(b + 1) * sizeof(float2);   // L and D of one system
+    size_t freeb = 0, total = 0;
+    if (cudaMemGetInfo(&freeb, &total) != cudaSuccess) return 0;
+    // buffers that this solve may reallocate count as free
+    const size_t avail = freeb + h->ws_L_bytes + h->ws_D_bytes + h->ws_Lt_bytes + h->ws_Dt_bytes;
+    const size_t fixed = (size_t)grid * per + (size_t)grid * (size_t)(b + 32) * (size_t)(b + 1) * sizeof(float2) +
+                         ((size_t)2 << 30);
+    if (avail <= fixed) return 0;
+    const long long kmax = (long long)((double)(avail - fixed) * 0.9 / (double)per);
+    if (kmax <= 0 || kmax >= n_t) return 0;
+    const long long waves = ((long long)n_t - kmax + grid - 1) / grid;
+    const long long K = (long long)n_t - waves * grid;
+    return K > 0 ? (int)K : 0;
+}
+
 bool factors_fit(st_fdm* h, size_t elem) {
     size_t freeb = 0, total = 0;
     if (cudaMemGetInfo(&freeb, &total) != cudaSuccess) return false;
@@ -220,7 +259,10 @@ bool factors_fit(st_fdm* h, size_t elem) {
 }
 
 // mode: 0 = factor and solve (factors transient, in chunks of systems), 1 = factor, keep all
-//       factors, and solve, 2 = forward + backward substitution with the kept factors
+//       factors, and solve, 2 = forward + backward substitution with the kept factors;
+//       partial keep (h->kept_sys systems kept, the rest refactorised in waves of one CTA each):
+//       3 = first application (the kept systems factorised into ws_L), 4 = later applications
+//       (substitutions for the kept systems)
 template <typename T>
 st_status band_run(st_fdm* h, C<T>* G, int mode, cudaStream_t st) {
     const SpaceMats& sm = h->sm;
@@ -243,8 +285,59 @@ st_status band_run(st_fdm* h, C<T>* G, int mode, cudaStream_t st) {
     a.status = h->ws_status;
     const int nbw = nb == 64 ? 32 : (nb < 0 ? -nb : nb);   // panel width of the selected kernel
     const size_t WR = (size_t)b + nbw;
+    if (mode == 3 || mode == 4) {
+        const int K = h->kept_sys;
+        if (K <= 0 || K >= n_t) return fail(ST_ERR_ARG, "spatial solve: kept-system count out of range");
+        if (mode == 4 && (!h->factors_valid || h->factors_prec != (int)sizeof(T)))
+            return fail(ST_ERR_ARG, "spatial solve: no stored factors");
+        st_status s = ST_OK;
+        if (mode == 3) {
+            // exactly K systems' worth: a larger buffer left by an earlier solve would hold memory
+            // that the choice of K counted as free
+            h->factors_valid = 0;
+            s = resize(h->ws_L, h->ws_L_bytes, (size_t)K * n * b * sizeof(C<T>), "kept band factors");
+            if (s != ST_OK) return s;
+            s = resize(h->ws_D, h->ws_D_bytes, (size_t)K * n * sizeof(C<T>), "kept band pivots");
+            if (s != ST_OK) return s;
+        }
+        s = grow(h->ws_win, h->ws_win_bytes, (size_t)grid * WR * (b + 1) * sizeof(C<T>), "band windows");
+        if (s != ST_OK) return s;
+        s = grow(h->ws_Lt, h->ws_Lt_bytes, (size_t)grid * n * b * sizeof(C<T>), "band factors");
+        if (s != ST_OK) return s;
+        s = grow(h->ws_Dt, h->ws_Dt_bytes, (size_t)grid * n * sizeof(C<T>), "band pivots");
+        if (s != ST_OK) return s;
+        a.win = reinterpret_cast<C<T>*>(h->ws_win);
+        // systems 0 .. K-1: factors stored per system k
+        a.L = reinterpret_cast<C<T>*>(h->ws_L);
+        a.D = reinterpret_cast<C<T>*>(h->ws_D);
+        a.keep = 1;
+        a.k0 = 0;
+        a.n_sys = K;
+        if (mode == 3) {
+            CUDA_TRY(band_factor_solve_launch<T>(a, nb, std::min(grid, K), st));
+        } else {
+            CUDA_TRY(subst_launch<T>(a, 0, K, true, st));
+        }
+        CUDA_TRY(subst_launch<T>(a, 0, K, false, st));
+        // systems K .. n_t-1: factor and solve, one wave of CTAs per launch, factors per CTA slot
+        a.L = reinterpret_cast<C<T>*>(h->ws_Lt);
+        a.D = reinterpret_cast<C<T>*>(h->ws_Dt);
+        a.keep = 0;
+        for (int k0 = K; k0 < n_t; k0 += grid) {
+            const int cnt = std::min(grid, n_t - k0);
+            a.k0 = k0;
+            a.n_sys = cnt;
+            CUDA_TRY(band_factor_solve_launch<T>(a, nb, cnt, st));
+            CUDA_TRY(subst_launch<T>(a, k0, cnt, false, st));
+        }
+        if (mode == 3) {
+            h->factors_valid = 1;
+            h->factors_prec = (int)sizeof(T);
+        }
+        return ST_OK;
+    }
     if (mode == 2) {
-        if (!h->factors_valid || h->factors_prec != (int)sizeof(T))
+        if (!h->factors_valid || h->factors_prec != (int)sizeof(T) || h->kept_sys != 0)
             return fail(ST_ERR_ARG, "spatial solve: no stored factors");
         a.win = nullptr;
         a.L = reinterpret_cast<C<T>*>(h->ws_L);
@@ -264,6 +357,7 @@ st_status band_run(st_fdm* h, C<T>* G, int mode, cudaStream_t st) {
     s = grow(h->ws_D, h->ws_D_bytes, (size_t)chunk * n * sizeof(C<T>), "band pivots");
     if (s != ST_OK) return s;
     h->factors_valid = 0;
+    h->kept_sys = 0;
     a.win = reinterpret_cast<C<T>*>(h->ws_win);
     a.L = reinterpret_cast<C<T>*>(h->ws_L);
     a.D = reinterpret_cast<C<T>*>(h->ws_D);
@@ -445,9 +539,10 @@ st_status precond32(st_fdm* h, bool adjoint, const double2* v, double2* z, bool&
     st_status s = xform32(h, adjoint ? XF_XT : XF_Y, v, true, scal, adjoint ? 1 : 0, G, false, 0, 0, nullptr, nullptr,
                           nullptr, nullptr, st);
     if (s != ST_OK) return s;
-    int mode = keep ? (first ? 1 : 2) : 0;
+    int mode = keep ? (first ? 1 : 2) : (h->kept_sys > 0 ? (first ? 3 : 4) : 0);
     s = band_run<float>(h, G, mode, st);
-    if (s == ST_ERR_OOM && mode == 1) {
+    if (s == ST_ERR_OOM && (mode == 1 || mode == 3)) {
+        h->kept_sys = 0;
         s = band_run<float>(h, G, 0, st);
         keep = false;
     }
@@ -508,6 +603,8 @@ st_status solve_mixed_gmres(st_fdm* h, bool adjoint, const void* F, const void* 
     }
     s = ensure_krylov(h, m);
     if (s != ST_OK) return s;
+    // when not all factors fit, keep those of as many systems as the memory left allows
+    h->kept_sys = (!keep && o.keep_factors == -1) ? partial_keep_count(h) : 0;
     double2* const* P = h->kry_ptrs;                 // device pointer array
     double2* V0 = reinterpret_cast<double2*>(h->ws_kry);
     auto Vp = [&](int i) { return V0 + (size_t)i * N; };
@@ -627,7 +724,7 @@ st_status solve_mixed_gmres(st_fdm* h, bool adjoint, const void* F, const void* 
     if (psi0 && !adjoint) CUDA_TRY(launch_add_row(n_t, n_x, psi, psi0, false, st));
     if (info) {
         info->sweeps = its;
-        info->factors_kept = keep ? 1 : 0;
+        info->factors_kept = keep ? 1 : (h->kept_sys > 0 ? 2 : 0);
         info->rel_residual = rel;
         for (int i = 0; i < 16; ++i) info->residual_history[i] = (i < nh) ? hist[i] : -1.0;
     }

@@ -230,6 +230,11 @@ struct st_fdm {
     CUtensorMap tc_mapB;
     void* ws_norm = nullptr;      // error-norm partial sums
     size_t ws_norm_bytes = 0;
-    int factors_valid = 0;        // ws_L holds the factors of all n_t systems (keep mode)
+    void* ws_Lt = nullptr;        // partial keep: factors of the systems refactorised every application
+    size_t ws_Lt_bytes = 0;
+    void* ws_Dt = nullptr;
+    size_t ws_Dt_bytes = 0;
+    int kept_sys = 0;             // partial keep: ws_L holds the factors of systems 0 .. kept_sys - 1
+    int factors_valid = 0;        // ws_L holds the factors of all n_t systems (keep mode) or of the kept ones
     int factors_prec = -1;
 };
