@@ -59,3 +59,30 @@ def test_reference_arm_json_line():
     assert line["cpu_baseline"]["kind"] == "oracle" and line["cpu_baseline"]["cores"] >= 1
     assert line["e2e"]["h2d_bytes_per_step"] == 0 and line["e2e"]["value"] == line["value"]
     assert line["higher_is_better"] is True and line["config"]["name"] == "c1"
+
+
+def test_recorded_traffic_is_keyed_on_kernel_source(tmp_path, monkeypatch):
+    """The committed DRAM traffic is reported only while the kernels' source is the one captured:
+    an edit to the factor section or the substitution kernels drops it to None, an edit to the
+    host-side handle struct does not."""
+    sys.path.insert(0, ROOT)
+    import shutil
+
+    import bench
+
+    assert bench.profiled_traffic("c2") is not None          # the committed capture matches the tree
+    root = tmp_path / "tree"
+    csrc = root / "paper_2504_07269_gb300" / "csrc"
+    csrc.mkdir(parents=True)
+    src = os.path.join(ROOT, "paper_2504_07269_gb300", "csrc")
+    for name in ("k_band.cu", "k_subst.cu", "async.cuh", "device.cuh"):
+        shutil.copy(os.path.join(src, name), csrc / name)
+    shutil.copytree(os.path.join(ROOT, "profiles"), root / "profiles")
+    monkeypatch.setattr(bench, "ROOT", str(root))
+    assert bench.profiled_traffic("c2") is not None
+    dev = (csrc / "device.cuh").read_text()
+    (csrc / "device.cuh").write_text(dev.replace("struct st_fdm {", "struct st_fdm {\n    int host_only_field = 0;", 1))
+    assert bench.profiled_traffic("c2") is not None          # host bookkeeping only
+    sub = (csrc / "k_subst.cu").read_text()
+    (csrc / "k_subst.cu").write_text(sub + "\n// edited\n")
+    assert bench.profiled_traffic("c2") is None               # kernel source changed
