@@ -596,12 +596,13 @@ __device__ __forceinline__ void band_bwd_cta(int n, int b, const float2* __restr
 #pragma unroll
         for (int cc = 0; cc < 4; ++cc) {
             const int j = j0 + warp * 4 + cc;
-            const int ohi = (j < j1) ? min(b, n - 1 - j) : -1;
+            // columns past the end of the block (j >= j1) read nothing: ohi = 0 < o
+            const int ohi = (j < j1) ? min(b, n - 1 - j) : 0;
             const float2* Lj = L + (size_t)j * b - 1;
 #pragma unroll
             for (int t = 0; t < NO; ++t) {
                 const int o = j1 - j + lane + 32 * t;
-                lv[cc][t] = (o <= ohi) ? Lj[o] : mk<T>(0, 0);
+                lv[cc][t] = (o >= 1 && o <= ohi) ? Lj[o] : mk<T>(0, 0);
             }
         }
     };
@@ -618,12 +619,12 @@ __device__ __forceinline__ void band_bwd_cta(int n, int b, const float2* __restr
 #pragma unroll
         for (int cc = 0; cc < 4; ++cc) {
             const int c = warp * 4 + cc, j = j0 + c;
-            const int ohi = (j < j1) ? min(b, n - 1 - j) : -1;
+            const int ohi = (j < j1) ? min(b, n - 1 - j) : 0;
             float2 acc = mk<T>(0, 0);
 #pragma unroll
             for (int t = 0; t < NO; ++t) {
                 const int o = j1 - j + lane + 32 * t;
-                if (o <= ohi) {
+                if (o >= 1 && o <= ohi) {
                     int r = j1m + lane + 32 * t;   // (j + o) % RB: j + o - j1 < b < RB
                     if (r >= RB) r -= RB;
                     cfma<T>(acc, lv[cc][t], ring[r]);
