@@ -12,6 +12,7 @@
 #include <vector>
 
 #include "device.cuh"
+#include "plan_rules.h"
 
 namespace stfdm {
 
@@ -224,10 +225,9 @@ const double2* shifts_of<double>(const st_fdm* h) { return h->s64; }
 template <>
 const float2* shifts_of<float>(const st_fdm* h) { return h->s32; }
 
-// Partial keep when not all complex64 factors fit: the number K of leading systems whose factors
-// stay in memory, as many as fit in 90% of the memory left after one wave of transient factors
-// (one system per resident CTA), rounded down so that the n_t - K systems refactorised at every
-// application fill whole waves (a wave costs the same whether full or not).  0 if none fit.
+// Partial keep when not all complex64 factors fit: the number of leading systems whose factors
+// stay in memory (partial_keep_systems), with one wave of transient factors (one system per
+// resident CTA), its windows and a 2 GiB reserve set aside.
 int partial_keep_count(st_fdm* h) {
     const int n_t = h->tm.n_t, n = h->sm.n_x, b = h->sm.m + 1;
     const int nb = band_pick_nb<float>(b, h->smem_optin);
@@ -242,12 +242,7 @@ int partial_keep_count(st_fdm* h) {
     const size_t avail = freeb + h->ws_L_bytes + h->ws_D_bytes + h->ws_Lt_bytes + h->ws_Dt_bytes;
     const size_t fixed = (size_t)grid * per + (size_t)grid * (size_t)(b + 32) * (size_t)(b + 1) * sizeof(float2) +
                          ((size_t)2 << 30);
-    if (avail <= fixed) return 0;
-    const long long kmax = (long long)((double)(avail - fixed) * 0.9 / (double)per);
-    if (kmax <= 0 || kmax >= n_t) return 0;
-    const long long waves = ((long long)n_t - kmax + grid - 1) / grid;
-    const long long K = (long long)n_t - waves * grid;
-    return K > 0 ? (int)K : 0;
+    return partial_keep_systems(n_t, grid, per, avail, fixed);
 }
 
 bool factors_fit(st_fdm* h, size_t elem) {

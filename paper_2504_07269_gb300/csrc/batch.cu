@@ -26,6 +26,7 @@
 #include <vector>
 
 #include "device.cuh"
+#include "plan_rules.h"
 
 namespace stfdm {
 
@@ -479,24 +480,18 @@ extern "C" st_status st_batch_create(st_fdm* const* hs, int count, const st_batc
     int m = o.restart > 0 ? std::min(o.restart, BATCH_MAX_RESTART) : BATCH_MAX_RESTART;
     m = std::min(m, kb_max_vectors() - 1);
     if (o.restart <= 0) {
-        // A kept factor saves a whole factorisation at every later application of its problem; a
-        // longer basis saves only restarts, and the FP32-preconditioned refinement converges within
-        // about ten applications whatever m is (64-problem batch: 331 applications at m = 13, 330 at
-        // m = 4, and 19% less time at m = 4 with 18 instead of 9 problems kept).  So the basis yields
-        // memory to the factors: the longest basis that leaves room for every keepable factor, but at
-        // least BATCH_MIN_RESTART vectors and at most half the free memory.
+        // The FP32-preconditioned refinement converges within about ten applications whatever m is
+        // (64-problem batch: 331 applications at m = 13, 330 at m = 4, and 19% less time at m = 4
+        // with 18 instead of 9 problems kept), so the basis yields memory to the kept factors.
         size_t freeb = 0, total = 0;
         cudaMemGetInfo(&freeb, &total);
         const size_t avail = freeb > fixed ? freeb - fixed : 0;
-        auto basis = [&](int mm) { return (size_t)N * ((mm + 1) * sizeof(double2) + mm * sizeof(float2)); };
-        while (m > 2 && basis(m) > avail / 2) --m;
         size_t factors = 0;
         if (!o.no_keep)
             for (int q = 0; q < P; ++q)
                 if (band[q].b <= 256)
                     factors += ((size_t)b->hprob[q].n_t * band[q].n * ((size_t)band[q].b + 1) * sizeof(float2) + 255) / 256 * 256;
-        const size_t room = avail > ((size_t)2 << 30) ? (size_t)((avail - ((size_t)2 << 30)) * 0.9) : 0;
-        while (m > BATCH_MIN_RESTART && basis(m) + factors > room) --m;
+        m = batch_restart_for_factors((size_t)N, avail, factors, m, BATCH_MIN_RESTART);
     }
     b->m = m;
     // device buffers
