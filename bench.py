@@ -1,17 +1,23 @@
 #!/usr/bin/env python
 """Benchmark: space-time unknowns/s of the mixed-precision refined FDM solve against the FP64 FDM.
 
-Workload (default): 256x256 squares P1 in space (65,025 interior nodes), P1 time on 512
-uniform elements, T = 1 (33,292,800 unknowns); manufactured psi = sin(pi x1) sin(pi x2)
-(1+t) e^{-it}; the load is the interpolated load (M_t,full (x) M_x) f of the nodal values
-of f = i d_t psi - Laplace psi (built on the device by st_load_nodal); psi0 = psi(., 0).
+Workload (default, `--config c3`): 384x384 squares P1 in space (146,689 interior nodes, half
+bandwidth 384), P2 time on 512 uniform elements (n_t = 1024), T = 2: 150,209,536 unknowns;
+psi0 = four seeded Gaussian wave packets, f = 0; mixed precision refined to a relative FP64
+residual of 1e-10.  The factors of all 1024 spatial systems (463 GB) do not fit in HBM: the
+leading systems' factors are kept, the others are refactorised at every FP32 application.
 
-One step = one full st_fdm_solve (lifting, forward transform, banded LDL^T factor and
-solve of all 512 spatial systems, back transform, FP64 residual, refinement sweeps until
-||R||/||F~|| <= 1e-11, see SINGLE_TOL).  The inputs (533 MB) exceed the 129 MB L2, so no
-flush is needed.
+`--config c2`: 256x256 squares P1 (65,025 nodes), P1 time on 512 uniform elements, T = 1
+(33,292,800 unknowns); manufactured psi = sin(pi x1) sin(pi x2) (1+t) e^{-it}, the interpolated
+load (M_t,full (x) M_x) f built on the device (st_load_nodal), psi0 = psi(., 0), refined to 1e-11.
 
-  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+One step = one H2D copy of the step's inputs (F, psi0) from pinned host memory, one full
+st_fdm_solve (lifting, forward transform, banded LDL^T factor and solve of the spatial systems,
+back transform, FP64 residual, refinement until the target), one D2H copy of psi.  CUDA events
+split every step: `value` counts the solve alone (its inputs resident in HBM), `e2e` the whole
+step.  The inputs (2.4 GB / 533 MB of c128) exceed the 129 MB L2, so no flush is needed.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--config c3|c2|c5]
 
 Multi-GPU: the single-problem workload does not shard without an exchange step; N ranks
 run N independent replicas (weak scaling), timed with a barrier and the max over ranks.
@@ -48,7 +54,7 @@ def parse_args(argv=None):
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--config", default="c2")
+    ap.add_argument("--config", default="c3")
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64", "fp32"])
     ap.add_argument("--no-fp64-check", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -184,22 +190,25 @@ def profiled_traffic(config: str):
 
 
 # ------------------------------------------------------------------ inputs
-def make_inputs(pr, device):
-    """Nodal values of the manufactured f at every DOF time (t_0 included) and psi0 = psi(., 0)."""
+def make_inputs(pr, h, device):
+    """The step's load F (c128, (n_t, n_x)) and psi0 on the device.  384^2/P2-1024 (c3): f = 0 and psi0
+    = four seeded packets; otherwise the manufactured psi of the 16^2/256^2 workloads: F is the
+    interpolated load (M_t,full (x) M_x) f of f's nodal values at every DOF time (st_load_nodal),
+    psi0 = psi(., 0)."""
     import torch
 
+    from paper_2504_07269_gb300 import stfdm
+
     x1, x2 = synth.interior_coords(pr.n, pr.Lx, pr.Ly)
-    # DOF times including t_0 (P1: the mesh nodes; P2: nodes and midpoints)
-    t = np.asarray(pr.t_nodes)
-    if pr.p_t == 1:
-        tf = t
-    else:
-        tf = np.empty(2 * len(t) - 1)
-        tf[0::2] = t
-        tf[1::2] = 0.5 * (t[:-1] + t[1:])
-    f = synth.f_c1(x1[None, :], x2[None, :], tf[:, None])
-    psi0 = synth.psi0_c1(x1, x2)
-    return torch.from_numpy(f).to(device), torch.from_numpy(psi0).to(device)
+    if pr.name == "c3":
+        psi0 = synth.packet_values(synth.packet_params(pr.seed), x1, x2)
+        F = torch.zeros((pr.n_t, pr.n_x), dtype=torch.complex128, device=device)
+        return F, torch.from_numpy(psi0).to(device)
+    tf = synth.dof_times(pr.p_t, pr.t_nodes)                 # t_0 included
+    f = torch.from_numpy(synth.f_c1(x1[None, :], x2[None, :], tf[:, None])).to(device)
+    F = stfdm.st_load_nodal(h, f)
+    del f
+    return F, torch.from_numpy(synth.psi0_c1(x1, x2)).to(device)
 
 
 # ------------------------------------------------------------------ CPU baseline (oracle)
@@ -250,18 +259,26 @@ def run_reference(args):
     return 0
 
 
-# Relative residual target of the single-problem mixed solve.  On the 256^2/512 workload the error
-# against the FP64 FDM is about 6x the final residual, so 1e-11 keeps it two orders below the
-# metric's 1e-9 bar (the line prints it); 1e-12 sits at the FP64 residual floor (the GMRES estimate
-# reaches 5e-13 while the true residual is 1.2e-12) and costs a second restart cycle.
-SINGLE_TOL = 1e-11
+# Relative residual target of the single-problem mixed solve per workload.  384^2/P2-1024: the
+# configuration's 1e-10.  256^2/512: on that workload the error against the FP64 FDM is about 6x the
+# final residual, so 1e-11 keeps it two orders below the metric's 1e-9 bar (the line prints it);
+# 1e-12 sits at the FP64 residual floor (the GMRES estimate reaches 5e-13 while the true residual is
+# 1.2e-12) and costs a second restart cycle.
+SINGLE_TOL = {"c3": 1e-10, "c2": 1e-11}
+
+
+def single_tol(pr):
+    return SINGLE_TOL.get(pr.name, 1e-11)
 
 
 def _config(pr, args):
+    inputs = ("psi0 = 4 seeded Gaussian packets, f = 0" if pr.name == "c3"
+              else "manufactured psi = sin(pi x1) sin(pi x2)(1+t)e^{-it}, interpolated load")
+    gb = pr.unknowns * 16 / 1e9
     return {"workload": f"{pr.n}x{pr.n} squares P1 space ({pr.n_x} nodes), P{pr.p_t} time {len(pr.t_nodes) - 1} "
-                        f"uniform elements (n_t={pr.n_t}), T={pr.t_nodes[-1]:g}; {pr.unknowns} unknowns",
-            "name": pr.name, "precision": args.precision, "tol": SINGLE_TOL, "n_x": pr.n_x, "n_t": pr.n_t,
-            "unknowns": pr.unknowns, "l2_flush": "inputs (533 MB c128 load) larger than the 129 MB L2",
+                        f"uniform elements (n_t={pr.n_t}), T={pr.t_nodes[-1]:g}; {pr.unknowns} unknowns; {inputs}",
+            "name": pr.name, "precision": args.precision, "tol": single_tol(pr), "n_x": pr.n_x, "n_t": pr.n_t,
+            "unknowns": pr.unknowns, "l2_flush": f"inputs ({gb:.2f} GB c128 load) larger than the 129 MB L2",
             "parallelism": "replicas" if args.gpus > 1 else "single GPU"}
 
 
@@ -279,12 +296,11 @@ def run_ours(args):
     from paper_2504_07269_gb300 import stfdm
 
     pr = synth.config_problem(args.config)
+    tol = single_tol(pr)
     t0 = time.perf_counter()
     h = stfdm.setup_problem(pr.n, pr.p_t, pr.t_nodes, Lx=pr.Lx, Ly=pr.Ly, device=local)
     setup_s = time.perf_counter() - t0
-    f_nodal, p0 = make_inputs(pr, dev)
-    F = stfdm.st_load_nodal(h, f_nodal)
-    del f_nodal
+    F, p0 = make_inputs(pr, h, dev)
     dt = torch.complex64 if args.precision == "fp32" else torch.complex128
     F = F.to(dt)
     p0 = p0.to(dt)
@@ -297,80 +313,68 @@ def run_ours(args):
             print(json.dumps({"profile_xform": args.config, "norm": float(torch.linalg.vector_norm(G32))}))
         return 0
     if args.profile_step:
-        _, info = stfdm.st_fdm_solve(h, F, p0, psi=psi, precision=args.precision, tol=SINGLE_TOL)
+        _, info = stfdm.st_fdm_solve(h, F, p0, psi=psi, precision=args.precision, tol=tol)
         torch.cuda.synchronize()
         if rank == 0:
             print(json.dumps({"profile_step": args.config, "precision": args.precision, "info": info}))
         return 0
 
-    def step():
+    # One step: H2D of the inputs from pinned host memory, the solve (inputs resident), D2H of psi.
+    # Four events per step on the launching stream split it into copy-in, solve and copy-out.
+    Fh = F.cpu().pin_memory()
+    p0h = p0.cpu().pin_memory()
+    psih = torch.empty(F.shape, dtype=dt).pin_memory()
+    h2d = Fh.numel() * Fh.element_size() + p0h.numel() * p0h.element_size()
+    d2h = psih.numel() * psih.element_size()
+    Fd = F
+    p0d = p0
+
+    def step(ev):
         nonlocal info
-        _, info = stfdm.st_fdm_solve(h, F, p0, psi=psi, precision=args.precision, tol=SINGLE_TOL)
+        ev[0].record()
+        Fd.copy_(Fh, non_blocking=True)
+        p0d.copy_(p0h, non_blocking=True)
+        ev[1].record()
+        _, info = stfdm.st_fdm_solve(h, Fd, p0d, psi=psi, precision=args.precision, tol=tol)
+        ev[2].record()
+        psih.copy_(psi, non_blocking=True)
+        ev[3].record()
+
+    def events():
+        return [torch.cuda.Event(enable_timing=True) for _ in range(4)]
 
     for _ in range(args.warmup):
-        step()
+        step(events())
     torch.cuda.synchronize()
     clk = ClockSampler(local)
     clk.start()
     barrier(world)
     torch.cuda.synchronize()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record()
-    for _ in range(args.steps):
-        step()
-    e1.record()
+    evs = [events() for _ in range(args.steps)]
+    for i in range(args.steps):
+        step(evs[i])
     torch.cuda.synchronize()
     barrier(world)
     clocks = clk.stop()
-    t_ms = e0.elapsed_time(e1) / args.steps
-    t_ms = reduce_max(t_ms, world, dev)
+    solve_ms = [e[1].elapsed_time(e[2]) for e in evs]
+    step_ms = [e[0].elapsed_time(e[3]) for e in evs]
+    h2d_ms = statistics.mean(e[0].elapsed_time(e[1]) for e in evs)
+    d2h_ms = statistics.mean(e[2].elapsed_time(e[3]) for e in evs)
+    t_ms = reduce_max(statistics.mean(solve_ms), world, dev)
+    e2e_ms = reduce_max(statistics.mean(step_ms), world, dev)
     value = world * pr.unknowns / (t_ms * 1e-3)
     sweeps = int(info.get("sweeps", 1)) if info else 1
-    # our kernels per step: the library counts the launches each solve issues (the ncu launch list of
-    # one step, profiles/launches_mixed_c2.md, agrees with it)
+    # our kernels per step: the library counts the launches each solve issues (an ncu launch list of
+    # one step agrees with it); the copies are not kernels
     launches_per_step = int(info.get("kernel_launches", 0)) if info else 0
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
 
-    # ---- end to end through the C ABI with host buffers (H2D of F and psi0, D2H of psi)
-    Fh = F.cpu().pin_memory()
-    p0h = p0.cpu().pin_memory()
-    psih = torch.empty(F.shape, dtype=dt).pin_memory()
-    Fd = torch.empty_like(F)
-    p0d = torch.empty_like(p0)
-
-    def e2e_step():
-        Fd.copy_(Fh, non_blocking=True)
-        p0d.copy_(p0h, non_blocking=True)
-        stfdm.st_fdm_solve(h, Fd, p0d, psi=psi, precision=args.precision, tol=SINGLE_TOL, want_info=False)
-        psih.copy_(psi, non_blocking=True)
-
-    e2e_step()
-    torch.cuda.synchronize()
-    barrier(world)
-    e0.record()
-    for _ in range(args.steps):
-        e2e_step()
-    e1.record()
-    torch.cuda.synchronize()
-    e2e_ms = reduce_max(e0.elapsed_time(e1) / args.steps, world, dev)
-    h2d = Fh.numel() * Fh.element_size() + p0h.numel() * p0h.element_size()
-    d2h = psih.numel() * psih.element_size()
-
-    # ---- error against the FP64 FDM on the same inputs
-    err = None
+    # ---- error against the FP64 FDM on the same inputs, and against a tightly refined solution
+    err = err_tight = fp64_res = None
     fp64_value = None
     fp32_value = fp32_err = None
     if not args.no_fp64_check and args.precision != "fp64":
-        ref = torch.empty(F.shape, dtype=torch.complex128, device=dev)
-        F64, p064 = F.to(torch.complex128), p0.to(torch.complex128)
-        stfdm.st_fdm_solve(h, F64, p064, psi=ref, precision="fp64")
-        torch.cuda.synchronize()
-        e0.record()
-        stfdm.st_fdm_solve(h, F64, p064, psi=ref, precision="fp64", want_info=False)
-        e1.record()
-        torch.cuda.synchronize()
-        fp64_value = pr.unknowns / (e0.elapsed_time(e1) * 1e-3)
-        stfdm.st_fdm_solve(h, F, p0, psi=psi, precision=args.precision, tol=SINGLE_TOL, want_info=False)
-        err = float(torch.linalg.vector_norm(psi.to(torch.complex128) - ref) / torch.linalg.vector_norm(ref))
+        mine = psi.to(torch.complex128)
         # the plain complex-FP32 FDM on the same inputs (3xTF32 tensor-core transforms, FP32 solves)
         F32, p032 = F.to(torch.complex64), p0.to(torch.complex64)
         psi32 = torch.empty_like(F32)
@@ -381,8 +385,27 @@ def run_ours(args):
         e1.record()
         torch.cuda.synchronize()
         fp32_value = pr.unknowns / (e0.elapsed_time(e1) * 1e-3)
-        fp32_err = float(torch.linalg.vector_norm(psi32.to(torch.complex128) - ref) / torch.linalg.vector_norm(ref))
-        del ref, F64, p064, F32, p032, psi32
+        del F32, p032
+        # the FP64 FDM (one solve: at the 384^2/P2-1024 workload it takes minutes)
+        ref = torch.empty(F.shape, dtype=torch.complex128, device=dev)
+        F64, p064 = F.to(torch.complex128), p0.to(torch.complex128)
+        torch.cuda.synchronize()
+        e0.record()
+        stfdm.st_fdm_solve(h, F64, p064, psi=ref, precision="fp64", want_info=False)
+        e1.record()
+        torch.cuda.synchronize()
+        fp64_value = pr.unknowns / (e0.elapsed_time(e1) * 1e-3)
+        nref = torch.linalg.vector_norm(ref)
+        err = float(torch.linalg.vector_norm(mine - ref) / nref)
+        fp32_err = float(torch.linalg.vector_norm(psi32.to(torch.complex128) - ref) / nref)
+        del psi32
+        fp64_res = float(stfdm.st_residual(h, F64, p064, ref)[0])
+        # the FP64 FDM carries the rounding of X_t (about kappa_2(X_t) eps in the residual): a solution
+        # refined to 1e-13 says which of the two is off
+        stfdm.st_fdm_solve(h, F64, p064, psi=ref, precision="mixed", tol=1e-13, max_sweeps=80, want_info=False)
+        err_tight = float(torch.linalg.vector_norm(mine - ref) / torch.linalg.vector_norm(ref))
+        del ref, mine, F64, p064
+        torch.cuda.empty_cache()
 
     # ---- roofline of the dominant kernel: the banded LDL^T factor-and-solve (FP32 / FP64)
     kprec = "fp64" if args.precision == "fp64" else "fp32"
@@ -426,13 +449,20 @@ def run_ours(args):
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": t_ms, "higher_is_better": True, "scaling": "weak",
                 "vs_baseline": None, "dtype": {"mixed": "c64+f64", "fp64": "f64", "fp32": "f32"}[args.precision],
-                "data": "synthetic (manufactured solution, interpolated load)", "config": _config(pr, args),
-                "err_vs_fp64": err, "fp64_fdm_unknowns_per_s": fp64_value,
+                "data": ("synthetic (seeded Gaussian packets, f = 0)" if pr.name == "c3"
+                         else "synthetic (manufactured solution, interpolated load)"),
+                "config": _config(pr, args),
+                "err_vs_fp64": err, "fp64_fdm_rel_residual": fp64_res, "err_vs_refined_1e-13": err_tight,
+                "fp64_fdm_unknowns_per_s": fp64_value,
                 "fp32_fdm_unknowns_per_s": fp32_value, "fp32_fdm_err_vs_fp64": fp32_err, "sweeps": sweeps,
+                "restart": info.get("restart") if info else None,
+                "kept_systems": info.get("kept_systems") if info else None,
                 "final_rel_residual": info.get("rel_residual") if info else None,
                 "setup_s": setup_s, "kappa_x": h.kappa,
                 "e2e": {"value": world * pr.unknowns / (e2e_ms * 1e-3), "unit": UNIT, "h2d_bytes_per_step": h2d,
-                        "d2h_bytes_per_step": d2h},
+                        "d2h_bytes_per_step": d2h, "h2d_ms": h2d_ms, "d2h_ms": d2h_ms,
+                        "h2d_gbs": h2d / (h2d_ms * 1e6), "d2h_gbs": d2h / (d2h_ms * 1e6),
+                        "timing": "same steps as value: events around H2D + solve + D2H (e2e) and the solve (value)"},
                 "gpu_launches": launches_per_step * args.steps,
                 "roofline": roof, "cpu_baseline": cpu, "clocks": clocks}
         print(json.dumps(line))

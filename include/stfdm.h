@@ -117,13 +117,16 @@ typedef struct {
     double setup_seconds;        /* host time of st_fdm_setup's FP64 decomposition */
     int tensor_cores;            /* 1 if the complex-FP32 time transforms ran on the tcgen05 tensor cores */
     int kernel_launches;         /* kernels this call launched (st_fdm_solve, st_adjoint_solve; 0 in batched solves) */
+    int restart;                 /* ST_MIXED with GMRES: the restart length m used (0 otherwise) */
+    int kept_systems;            /* ST_MIXED: spatial systems whose factors stayed in memory across
+                                    applications (n_t when all were kept, 0 when none) */
 } st_solve_info;
 
 /* ------------------------------------------------------------------ status */
 const char* st_status_string(st_status s);
 const char* st_last_error_message(void);
 int st_abi_version(void);   /* returns STFDM_ABI_VERSION of the built library */
-#define STFDM_ABI_VERSION 4
+#define STFDM_ABI_VERSION 5
 
 /* ------------------------------------------------------------------ assembly (host) */
 /* Temporal matrices of eq. (matrix_t), Section 3.  p_t in {1, 2}: continuous piecewise
@@ -173,7 +176,8 @@ st_status st_fdm_solve(st_fdm* h, const void* F, const void* psi0, void* psi,
                        const st_solve_opts* opts, st_solve_info* info, void* stream);
 
 /* FP64 Kronecker residual R = F~ - K (psi - 1 (x) psi0) with F~ = F - m_t (x) A_x psi0
- * (eq. LGS; c128 arrays, psi0 may be NULL).  R may be NULL (norm only).  rel_norm (host, may be
+ * (eq. LGS; c128 arrays, psi0 may be NULL).  R may be NULL (norm only); it may alias F but not psi
+ * or psi0 (ST_ERR_ARG).  rel_norm (host, may be
  * NULL) receives ||R||_2 / ||F~||_2; when it is non-NULL the call synchronises the stream. */
 st_status st_residual(st_fdm* h, const void* F, const void* psi0, const void* psi, void* R,
                       double* rel_norm, void* stream);
@@ -312,7 +316,7 @@ st_status st_load_quadrature(st_fdm* h, int exact, int q_t, int q_x, void* F, vo
  * that cannot take cudaMalloc's implicit device synchronisation.  It has no counterpart in the
  * paper; it computes the same R = F~ - K (psi - 1 (x) psi0) as st_residual.
  * F, psi: device (n_t, n_x) c128; psi0: device n_x c128 or NULL; R: device (n_t, n_x) c128 output
- * or NULL; norms: device double[2] output receiving ||R||_2^2 and ||F~||_2^2 (the caller divides;
+ * or NULL (it may alias F but not psi or psi0: ST_ERR_ARG); norms: device double[2] output receiving ||R||_2^2 and ||F~||_2^2 (the caller divides;
  * nothing is copied to the host and the call never synchronises).
  * It calls no allocating routine: its only scratch is a fixed 1 MiB array of per-block partial
  * sums inside the library, resident on every device that loads it until the process exits.  The
@@ -323,6 +327,18 @@ st_status st_load_quadrature(st_fdm* h, int exact, int q_t, int q_x, void* F, vo
  * host threads) race and must be serialised by the caller. */
 st_status st_residual_noalloc(const st_fdm* h, const void* F, const void* psi0, const void* psi, void* R,
                               double* norms, void* stream);
+
+/* ------------------------------------------------------------------ failure detection */
+/* Test hook for the bounded device-side waits (no counterpart in the paper).  Every asynchronous
+ * pipeline in the library waits on shared-memory mbarriers with a time limit, after which the CTA
+ * records an error, lets the copies it has in flight land and returns, and the entry point reports
+ * ST_ERR_TIMEOUT instead of hanging.  With seconds > 0, every later substitution launch of the
+ * handle (the backward substitution of st_spatial_solve, the substitutions of the solves) makes its
+ * copy-issuing thread first wait, for at most `seconds`, on an mbarrier that receives neither a
+ * copy nor an arrival: the wait runs out before any copy is issued, the kernel takes its timeout
+ * exit and the entry point returns ST_ERR_TIMEOUT.  seconds = 0 (the default) turns the probe off;
+ * the handle stays usable.  Errors: ST_ERR_ARG (NULL handle, seconds outside [0, 1]). */
+st_status st_set_wait_probe(st_fdm* h, double seconds);
 
 /* ------------------------------------------------------------------ teardown */
 void st_destroy_time(st_time* t);

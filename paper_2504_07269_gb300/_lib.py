@@ -52,7 +52,8 @@ class st_solve_opts(ctypes.Structure):
 class st_solve_info(ctypes.Structure):
     _fields_ = [("sweeps", c_int), ("factors_kept", c_int), ("rel_residual", c_double),
                 ("residual_history", c_double * 16), ("kappa_x", c_double), ("min_neg_im_shift", c_double),
-                ("setup_seconds", c_double), ("tensor_cores", c_int), ("kernel_launches", c_int)]
+                ("setup_seconds", c_double), ("tensor_cores", c_int), ("kernel_launches", c_int),
+                ("restart", c_int), ("kept_systems", c_int)]
 
 
 class st_batch_opts(ctypes.Structure):
@@ -104,6 +105,7 @@ SIGNATURES = {
     "st_error_norms": (c_int, [c_void_p, c_int, c_void_p, c_void_p, c_int, c_int, ctypes.POINTER(c_double), c_void_p]),
     "st_load_quadrature": (c_int, [c_void_p, c_int, c_int, c_int, c_void_p, c_void_p]),
     "st_residual_noalloc": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]),
+    "st_set_wait_probe": (c_int, [c_void_p, c_double]),
     "st_destroy_time": (None, [c_void_p]),
     "st_destroy_space": (None, [c_void_p]),
     "st_destroy_fdm": (None, [c_void_p]),

@@ -228,21 +228,29 @@ const float2* shifts_of<float>(const st_fdm* h) { return h->s32; }
 // Partial keep when not all complex64 factors fit: the number of leading systems whose factors
 // stay in memory (partial_keep_systems), with one wave of transient factors (one system per
 // resident CTA), its windows and a 2 GiB reserve set aside.
-int partial_keep_count(st_fdm* h) {
+// One wave of transient factors: grid = resident CTAs of the complex64 factor kernel, per = bytes
+// of one system's L and D, fixed = the wave's factors, its windows and a 2 GiB reserve.
+bool partial_keep_geometry(const st_fdm* h, int& grid, size_t& per, size_t& fixed) {
     const int n_t = h->tm.n_t, n = h->sm.n_x, b = h->sm.m + 1;
     const int nb = band_pick_nb<float>(b, h->smem_optin);
-    if (nb == 0) return 0;
+    if (nb == 0) return false;
     int occ = band_occupancy<float>(nb, b);
     if (occ < 1) occ = 1;
-    const int grid = std::max(1, std::min(n_t, occ * h->sm_count));
-    const size_t per = (size_t)n * (size_t)(b + 1) * sizeof(float2);   // L and D of one system
+    grid = std::max(1, std::min(n_t, occ * h->sm_count));
+    per = (size_t)n * (size_t)(b + 1) * sizeof(float2);
+    fixed = (size_t)grid * per + (size_t)grid * (size_t)(b + 32) * (size_t)(b + 1) * sizeof(float2) + ((size_t)2 << 30);
+    return true;
+}
+
+int partial_keep_count(st_fdm* h) {
+    int grid = 0;
+    size_t per = 0, fixed = 0;
+    if (!partial_keep_geometry(h, grid, per, fixed)) return 0;
     size_t freeb = 0, total = 0;
     if (cudaMemGetInfo(&freeb, &total) != cudaSuccess) return 0;
     // buffers that this solve may reallocate count as free
     const size_t avail = freeb + h->ws_L_bytes + h->ws_D_bytes + h->ws_Lt_bytes + h->ws_Dt_bytes;
-    const size_t fixed = (size_t)grid * per + (size_t)grid * (size_t)(b + 32) * (size_t)(b + 1) * sizeof(float2) +
-                         ((size_t)2 << 30);
-    return partial_keep_systems(n_t, grid, per, avail, fixed);
+    return partial_keep_systems(h->tm.n_t, grid, per, avail, fixed);
 }
 
 bool factors_fit(st_fdm* h, size_t elem) {
@@ -278,6 +286,7 @@ st_status band_run(st_fdm* h, C<T>* G, int mode, cudaStream_t st) {
     a.shifts = shifts_of<T>(h);
     a.rhs = G;
     a.status = h->ws_status;
+    a.probe_ns = h->wait_probe_ns;
     const int nbw = nb == 64 ? 32 : (nb < 0 ? -nb : nb);   // panel width of the selected kernel
     const size_t WR = (size_t)b + nbw;
     if (mode == 3 || mode == 4) {
@@ -511,6 +520,7 @@ st_status solve_mixed(st_fdm* h, bool adjoint, const void* F, const void* psi0, 
     if (info) {
         info->sweeps = sweeps;
         info->factors_kept = keep ? 1 : 0;
+        info->kept_systems = keep ? n_t : 0;
         info->rel_residual = rel;
         for (int i = 0; i < 16; ++i) info->residual_history[i] = (i < nh) ? hist[i] : -1.0;
     }
@@ -547,10 +557,12 @@ st_status precond32(st_fdm* h, bool adjoint, const double2* v, double2* z, bool&
                    nullptr, nullptr, st);
 }
 
-st_status ensure_krylov(st_fdm* h, int m) {
+// exact: reallocate unless the size matches (memory planned for kept factors must really be free)
+st_status ensure_krylov(st_fdm* h, int m, bool exact = false) {
     const size_t N = (size_t)h->tm.n_t * h->sm.n_x;
     const size_t need = (size_t)(2 * m + 1) * N * sizeof(double2);
-    st_status s = grow(h->ws_kry, h->ws_kry_bytes, need, "GMRES basis");
+    st_status s = exact ? resize(h->ws_kry, h->ws_kry_bytes, need, "GMRES basis")
+                        : grow(h->ws_kry, h->ws_kry_bytes, need, "GMRES basis");
     if (s != ST_OK) return s;
     if (!h->kry_ptrs) {
         s = dev_alloc(reinterpret_cast<void**>(&h->kry_ptrs), sizeof(double2*) * 2 * (krylov_max_vectors() + 1),
@@ -584,8 +596,11 @@ st_status solve_mixed_gmres(st_fdm* h, bool adjoint, const void* F, const void* 
     bool keep = false;
     if (o.keep_factors == 1) keep = true;
     else if (o.keep_factors == -1) keep = factors_fit(h, sizeof(float2));
-    // restart length: at most 20, and the basis within a quarter of the free memory
+    // restart length: at most 20, and the basis within a third of the free memory; when not all
+    // factors fit (partial keep), the longest basis that costs no refactorisation wave more than the
+    // shortest (4 vectors) would
     int m = std::min(20, krylov_max_vectors() - 1);
+    const bool partial_keep = !keep && o.keep_factors == -1;
     {
         size_t freeb = 0, total = 0;
         cudaMemGetInfo(&freeb, &total);
@@ -594,12 +609,19 @@ st_status solve_mixed_gmres(st_fdm* h, bool adjoint, const void* F, const void* 
             const size_t fac = (size_t)n_t * n_x * (size_t)(h->sm.m + 2) * sizeof(float2);
             avail = avail > fac + h->ws_L_bytes ? avail - (fac > h->ws_L_bytes ? fac - h->ws_L_bytes : 0) : 0;
         }
-        while (m > 2 && (size_t)(2 * m + 1) * N * sizeof(double2) > avail / 3) --m;
+        int grid = 0;
+        size_t per = 0, fixed = 0;
+        if (partial_keep && partial_keep_geometry(h, grid, per, fixed)) {
+            avail += h->ws_L_bytes + h->ws_D_bytes + h->ws_Lt_bytes + h->ws_Dt_bytes;
+            m = single_restart_for_partial_keep(N, n_t, grid, per, avail, fixed, m, 4);
+        } else {
+            while (m > 2 && (size_t)(2 * m + 1) * N * sizeof(double2) > avail / 3) --m;
+        }
     }
-    s = ensure_krylov(h, m);
+    s = ensure_krylov(h, m, partial_keep);
     if (s != ST_OK) return s;
     // when not all factors fit, keep those of as many systems as the memory left allows
-    h->kept_sys = (!keep && o.keep_factors == -1) ? partial_keep_count(h) : 0;
+    h->kept_sys = partial_keep ? partial_keep_count(h) : 0;
     double2* const* P = h->kry_ptrs;                 // device pointer array
     double2* V0 = reinterpret_cast<double2*>(h->ws_kry);
     auto Vp = [&](int i) { return V0 + (size_t)i * N; };
@@ -720,6 +742,8 @@ st_status solve_mixed_gmres(st_fdm* h, bool adjoint, const void* F, const void* 
     if (info) {
         info->sweeps = its;
         info->factors_kept = keep ? 1 : (h->kept_sys > 0 ? 2 : 0);
+        info->restart = m;
+        info->kept_systems = keep ? n_t : h->kept_sys;
         info->rel_residual = rel;
         for (int i = 0; i < 16; ++i) info->residual_history[i] = (i < nh) ? hist[i] : -1.0;
     }
@@ -773,6 +797,8 @@ void fill_info_common(const st_fdm* h, st_solve_info* info, int precision) {
     info->min_neg_im_shift = h->td.min_neg_im;
     info->setup_seconds = h->setup_seconds;
     info->tensor_cores = (precision != ST_FP64 && h->tc_ok) ? 1 : 0;
+    info->restart = 0;
+    info->kept_systems = 0;
 }
 
 }  // namespace
@@ -960,6 +986,8 @@ extern "C" st_status st_fdm_solve(st_fdm* h, const void* F, const void* psi0, vo
 extern "C" st_status st_residual(st_fdm* h, const void* F, const void* psi0, const void* psi, void* R,
                                  double* rel_norm, void* stream) {
     if (!h || !F || !psi) return fail(ST_ERR_ARG, "st_residual: NULL argument");
+    // R is written while other threads still read the stencil neighbours of psi and psi0
+    if (R && (R == psi || R == psi0)) return fail(ST_ERR_ARG, "st_residual: R must not alias psi or psi0");
     DeviceGuard g(h->device);
     cudaStream_t st = S(stream);
     st_status s = ensure_common(h);
@@ -1080,3 +1108,10 @@ extern "C" st_status st_load_nodal(st_fdm* h, const void* f_nodal, void* F, void
     return ST_OK;
 }
 
+
+extern "C" st_status st_set_wait_probe(st_fdm* h, double seconds) {
+    if (!h) return fail(ST_ERR_ARG, "st_set_wait_probe: NULL handle");
+    if (!(seconds >= 0.0) || seconds > 1.0) return fail(ST_ERR_ARG, "st_set_wait_probe: seconds must be in [0, 1]");
+    h->wait_probe_ns = (unsigned long long)(seconds * 1e9);
+    return ST_OK;
+}

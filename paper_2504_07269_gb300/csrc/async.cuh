@@ -49,6 +49,18 @@ __device__ __forceinline__ bool bar_wait(uint64_t* bar, uint32_t parity, uint64_
         if (global_ns() - t0 > limit_ns) return false;
     }
 }
+// The same wait, also ending (false) as soon as *abort becomes non-zero (another role of the CTA
+// gave up).
+__device__ __forceinline__ bool bar_wait_or_abort(uint64_t* bar, uint32_t parity, uint64_t limit_ns,
+                                                  const volatile int* abort) {
+    if (bar_try_wait(bar, parity)) return true;
+    const uint64_t t0 = global_ns();
+    for (;;) {
+        if (bar_try_wait(bar, parity)) return true;
+        if (*abort) return false;
+        if (global_ns() - t0 > limit_ns) return false;
+    }
+}
 // bytes (a multiple of 16) from global src to shared dst (both 16-byte aligned), completing
 // `bytes` of the transaction count of `bar`
 __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {

@@ -99,6 +99,8 @@ struct BandArgs {
     C<T>* D;              // pivots
     int keep;             // 1: factors stored per system k, 0: per system of this launch (slot k - k0)
     int* status;          // status[0] set to 1 on a zero / non-finite pivot
+    unsigned long long probe_ns = 0;   // > 0: substitution producers first wait this long on a barrier
+                                       // that nothing completes (test of the bounded waits)
 };
 // panel width code: the panel width (32/16/8), negative for the unstaged complex64 kernel, 0 = too wide
 template <typename T> int band_pick_nb(int b, size_t smem_optin);
@@ -237,4 +239,5 @@ struct st_fdm {
     int kept_sys = 0;             // partial keep: ws_L holds the factors of systems 0 .. kept_sys - 1
     int factors_valid = 0;        // ws_L holds the factors of all n_t systems (keep mode) or of the kept ones
     int factors_prec = -1;
+    unsigned long long wait_probe_ns = 0;   // st_set_wait_probe: copied into the substitution launches
 };

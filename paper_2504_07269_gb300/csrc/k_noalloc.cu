@@ -166,6 +166,8 @@ using namespace stfdm;
 extern "C" st_status st_residual_noalloc(const st_fdm* h, const void* F, const void* psi0, const void* psi, void* R,
                                          double* norms, void* stream) {
     if (!h || !F || !psi || !norms) return fail(ST_ERR_ARG, "st_residual_noalloc: NULL argument");
+    // R is written while other threads still read the stencil neighbours of psi and psi0
+    if (R && (R == psi || R == psi0)) return fail(ST_ERR_ARG, "st_residual_noalloc: R must not alias psi or psi0");
     const int n_t = h->tm.n_t, n_x = h->sm.n_x;
     const dim3 grid((n_x + NOALLOC_THREADS - 1) / NOALLOC_THREADS, (n_t + NOALLOC_ROWS - 1) / NOALLOC_ROWS);
     const size_t nblocks = (size_t)grid.x * grid.y;
@@ -190,6 +192,7 @@ extern "C" st_status st_residual_noalloc(const st_fdm* h, const void* F, const v
         if (e == cudaSuccess) {
             k_noalloc_finalize<<<1, 256, 0, cs>>>(partials, (int)nblocks, norms);
             e = cudaGetLastError();
+            if (e == cudaSuccess) note_launches(2);
         }
         if (e != cudaSuccess) s = fail(ST_ERR_CUDA, std::string("st_residual_noalloc: launch: ") + cudaGetErrorString(e));
     }

@@ -36,6 +36,7 @@ constexpr unsigned long long SUB_WAIT_NS = 2000000000ull;   // 2 s per wait
 struct SubShared {
     uint64_t full[SUB_STAGES];
     uint64_t empty[SUB_STAGES];
+    uint64_t never;  // initialised, never arrived on: the target of the wait probe
     int err;
     int issued;      // bulk copies issued by the producer
     int consumed;    // stages released by the consumer
@@ -57,6 +58,7 @@ struct SingleSrc {
     BandArgs<T> a;
     int k0, nsys;
     __device__ int count() const { return nsys; }
+    __device__ unsigned long long probe_ns() const { return a.probe_ns; }
     __device__ SubSys<T> get(int ks) const {
         const int k = k0 + ks;
         const size_t slot = a.keep ? (size_t)k : (size_t)ks;
@@ -73,6 +75,7 @@ struct GroupSrc {
     const int* active;
     const int* factored;
     __device__ int count() const { return n_items; }
+    __device__ unsigned long long probe_ns() const { return 0; }
     __device__ SubSys<float> get(int ks) const {
         const int2 pk = items[ks];
         const BatchBand& pb = probs[pk.x];
@@ -88,6 +91,13 @@ struct GroupSrc {
 template <typename T, int G, bool FWD, typename Src>
 __device__ void subst_produce(const Src& src, int sb, C<T>* ring, SubShared* sh) {
     int it = 0;
+    // wait probe: a wait on a barrier that receives no copy and no arrival runs out, and the CTA
+    // takes the same exit as on a real timeout (nothing has been issued yet)
+    if (src.probe_ns() > 0 && !async::bar_wait(&sh->never, 0, src.probe_ns())) {
+        atomicExch(&sh->err, 1);
+        sh->issued = 0;
+        return;
+    }
     for (int ks = blockIdx.x; ks < src.count(); ks += gridDim.x) {
         const SubSys<T> sys = src.get(ks);
         if (sys.n == 0) continue;
@@ -127,6 +137,7 @@ __device__ void subst_setup(SubShared* sh) {
             async::bar_init(&sh->full[s], 1);
             async::bar_init(&sh->empty[s], 1);
         }
+        async::bar_init(&sh->never, 1);
         sh->err = 0;
         sh->issued = 0;
         sh->consumed = 0;
@@ -171,7 +182,7 @@ __global__ void __launch_bounds__(64) k_subst_fwd(Src src, int sb, int* status) 
             for (int g = 0; g < ngroups; ++g, ++it) {
                 const int j0 = g * G, jb = j0 & ~31, l0 = j0 & 31;
                 const int s = it % SUB_STAGES;
-                if (!async::bar_wait(&sh->full[s], (it / SUB_STAGES) & 1, SUB_WAIT_NS)) {
+                if (!async::bar_wait_or_abort(&sh->full[s], (it / SUB_STAGES) & 1, SUB_WAIT_NS, &sh->err)) {
                     atomicExch(&sh->err, 1);
                     ok = false;
                     break;
@@ -260,7 +271,7 @@ __global__ void __launch_bounds__(64) k_subst_bwd(Src src, int sb, int* status) 
             for (int g = 0; g < ngroups; ++g, ++it) {
                 const int j0 = jtop - g * G, jb = j0 & ~31, l0 = j0 & 31;
                 const int s = it % SUB_STAGES;
-                if (!async::bar_wait(&sh->full[s], (it / SUB_STAGES) & 1, SUB_WAIT_NS)) {
+                if (!async::bar_wait_or_abort(&sh->full[s], (it / SUB_STAGES) & 1, SUB_WAIT_NS, &sh->err)) {
                     atomicExch(&sh->err, 1);
                     ok = false;
                     break;

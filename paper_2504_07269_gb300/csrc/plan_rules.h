@@ -37,4 +37,33 @@ inline int partial_keep_systems(int n_t, int grid, size_t per, size_t avail, siz
     return K > 0 ? (int)K : 0;
 }
 
+// GMRES basis of the single-problem refinement with restart length m over N unknowns: m + 1
+// complex128 basis vectors and m complex128 preconditioned directions.
+inline size_t single_basis_bytes(size_t N, int m) { return N * (size_t)(2 * m + 1) * 16; }
+
+// Waves of `grid` CTAs that refactorise the systems whose factors are not kept.
+inline int refactor_waves(int n_t, int grid, int kept) {
+    return grid > 0 ? (n_t - kept + grid - 1) / grid : 0;
+}
+
+// Restart length of the single-problem refinement when the factors of all n_t systems do not fit
+// (partial keep), starting from m (the longest allowed): first at most a third of `avail`, then
+// shortened (down to m_min) while a shorter basis would let so many more factors stay that a whole
+// wave of refactorisation drops from every preconditioner application.  The refinement converges
+// in about the same number of applications whatever the restart length, so a refactorisation wave
+// costs more than the restarts a longer basis saves.
+inline int single_restart_for_partial_keep(size_t N, int n_t, int grid, size_t per, size_t avail, size_t fixed,
+                                           int m, int m_min) {
+    while (m > 2 && single_basis_bytes(N, m) > avail / 3) --m;
+    if (m_min > m) m_min = m;
+    auto waves = [&](int mm) {
+        const size_t b = single_basis_bytes(N, mm);
+        const int K = b < avail ? partial_keep_systems(n_t, grid, per, avail - b, fixed) : 0;
+        return refactor_waves(n_t, grid, K);
+    };
+    const int best = waves(m_min);
+    while (m > m_min && waves(m) > best) --m;
+    return m;
+}
+
 }  // namespace stfdm

@@ -45,10 +45,11 @@ class SpaceHandle(_Handle):
 class FdmHandle(_Handle):
     _destroy = "st_destroy_fdm"
 
-    def __init__(self, ptr, time, space):
+    def __init__(self, ptr, time, space, device):
         super().__init__(ptr)
         self.time = time
         self.space = space
+        self.device = device      # CUDA ordinal the handle's device data live on
         n_t, n_x, m = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
         kap, mni = ctypes.c_double(), ctypes.c_double()
         check(lib().st_fdm_get(ptr, ctypes.byref(n_t), ctypes.byref(n_x), ctypes.byref(m), ctypes.byref(kap),
@@ -70,12 +71,20 @@ def _ptr(t):
     return ctypes.c_void_p(t.data_ptr()) if t is not None else None
 
 
+def _check_device(h: FdmHandle, t, name):
+    # the library launches on the handle's device: a tensor elsewhere would be read through a
+    # pointer that is not valid there
+    if t.device.index != h.device:
+        raise ValueError(f"{name}: tensor on {t.device}, but the handle lives on cuda:{h.device}")
+
+
 def _check_st(h: FdmHandle, t, dtype, name):
     if t is None:
         return
     if not t.is_cuda or t.dtype != dtype or not t.is_contiguous() or tuple(t.shape) != (h.n_t, h.n_x):
         raise ValueError(f"{name}: expected a contiguous CUDA {dtype} tensor of shape {(h.n_t, h.n_x)}, "
                          f"got {t.dtype} {tuple(t.shape)} on {t.device}")
+    _check_device(h, t, name)
 
 
 def _check_vec(h: FdmHandle, t, dtype, name):
@@ -83,6 +92,16 @@ def _check_vec(h: FdmHandle, t, dtype, name):
         return
     if not t.is_cuda or t.dtype != dtype or not t.is_contiguous() or tuple(t.shape) != (h.n_x,):
         raise ValueError(f"{name}: expected a contiguous CUDA {dtype} tensor of shape {(h.n_x,)}")
+    _check_device(h, t, name)
+
+
+def _check_no_alias(R, others, name="R"):
+    """R is written while other threads still read stencil neighbours of psi and psi0."""
+    if R is None:
+        return
+    for o in others:
+        if o is not None and o.data_ptr() == R.data_ptr():
+            raise ValueError(f"{name} must not alias psi or psi0")
 
 
 def _check_with_info(status, where, info):
@@ -111,7 +130,8 @@ def _info_dict(info: _lib.st_solve_info):
     return dict(sweeps=info.sweeps, factors_kept=info.factors_kept, rel_residual=info.rel_residual,
                 residual_history=[v for v in info.residual_history if v >= 0], kappa_x=info.kappa_x,
                 min_neg_im_shift=info.min_neg_im_shift, setup_seconds=info.setup_seconds,
-                tensor_cores=info.tensor_cores, kernel_launches=info.kernel_launches)
+                tensor_cores=info.tensor_cores, kernel_launches=info.kernel_launches, restart=info.restart,
+                kept_systems=info.kept_systems)
 
 
 # ------------------------------------------------------------------ assembly / setup
@@ -165,7 +185,7 @@ def st_fdm_setup(t: TimeHandle, s: SpaceHandle, kappa_max: float = 0.0, device: 
     opts = _lib.st_setup_opts(float(kappa_max), int(device), int(host_threads))
     out = ctypes.c_void_p()
     check(lib().st_fdm_setup(t.ptr, s.ptr, ctypes.byref(opts), ctypes.byref(out)), "st_fdm_setup")
-    return FdmHandle(out, t, s)
+    return FdmHandle(out, t, s, int(device) if device >= 0 else torch.cuda.current_device())
 
 
 # ------------------------------------------------------------------ solves
@@ -190,6 +210,7 @@ def st_residual(h: FdmHandle, F, psi0, psi, R=None, want_norm=True, stream=None)
     _check_st(h, psi, torch.complex128, "psi")
     _check_vec(h, psi0, torch.complex128, "psi0")
     _check_st(h, R, torch.complex128, "R")
+    _check_no_alias(R, (psi, psi0))
     rel = ctypes.c_double(-1.0)
     check(lib().st_residual(h.ptr, _ptr(F), _ptr(psi0), _ptr(psi), _ptr(R), ctypes.byref(rel) if want_norm else None,
                             _stream(stream)), "st_residual")
@@ -379,11 +400,19 @@ def st_residual_noalloc(h: FdmHandle, F, psi0, psi, R, norms, stream=None):
     _check_st(h, psi, torch.complex128, "psi")
     _check_vec(h, psi0, torch.complex128, "psi0")
     _check_st(h, R, torch.complex128, "R")
+    _check_no_alias(R, (psi, psi0))
     if not norms.is_cuda or norms.dtype != torch.float64 or norms.numel() < 2 or not norms.is_contiguous():
         raise ValueError("norms: expected a contiguous CUDA float64 tensor with 2 entries")
+    _check_device(h, norms, "norms")
     check(lib().st_residual_noalloc(h.ptr, _ptr(F), _ptr(psi0), _ptr(psi), _ptr(R), _ptr(norms), _stream(stream)),
           "st_residual_noalloc")
     return norms
+
+
+def st_set_wait_probe(h: FdmHandle, seconds: float):
+    """Test hook: later substitution launches first wait `seconds` on a barrier nothing completes
+    (the bounded-wait exit, ST_ERR_TIMEOUT); 0 turns it off."""
+    check(lib().st_set_wait_probe(h.ptr, float(seconds)), "st_set_wait_probe")
 
 
 def setup_problem(n_squares: int, p_t: int, t_nodes, Lx: float = 1.0, Ly: float = 1.0, **kw) -> FdmHandle:

@@ -62,27 +62,30 @@ def test_reference_arm_json_line():
 
 
 def test_recorded_traffic_is_keyed_on_kernel_source(tmp_path, monkeypatch):
-    """The committed DRAM traffic is reported only while the kernels' source is the one captured:
-    an edit to the factor section or the substitution kernels drops it to None, an edit to the
+    """Recorded DRAM traffic is reported only while the kernels' source is the one captured: an
+    edit to the factor section or the substitution kernels drops it to None, an edit to the
     host-side handle struct does not."""
     sys.path.insert(0, ROOT)
+    import json
     import shutil
 
     import bench
 
-    assert bench.profiled_traffic("c2") is not None          # the committed capture matches the tree
     root = tmp_path / "tree"
     csrc = root / "paper_2504_07269_gb300" / "csrc"
     csrc.mkdir(parents=True)
     src = os.path.join(ROOT, "paper_2504_07269_gb300", "csrc")
     for name in ("k_band.cu", "k_subst.cu", "async.cuh", "device.cuh"):
         shutil.copy(os.path.join(src, name), csrc / name)
-    shutil.copytree(os.path.join(ROOT, "profiles"), root / "profiles")
+    (root / "profiles").mkdir()
     monkeypatch.setattr(bench, "ROOT", str(root))
-    assert bench.profiled_traffic("c2") is not None
+    rec = {"band_factor_fp32_c3": {"k_band_sha": bench.kernel_source_sha(), "dram_bytes_per_launch": 1.0e12}}
+    (root / "profiles" / "traffic.json").write_text(json.dumps(rec))
+    assert bench.profiled_traffic("c3") == 1.0e12
+    assert bench.profiled_traffic("c2") is None               # no capture of that workload
     dev = (csrc / "device.cuh").read_text()
     (csrc / "device.cuh").write_text(dev.replace("struct st_fdm {", "struct st_fdm {\n    int host_only_field = 0;", 1))
-    assert bench.profiled_traffic("c2") is not None          # host bookkeeping only
+    assert bench.profiled_traffic("c3") == 1.0e12             # host bookkeeping only
     sub = (csrc / "k_subst.cu").read_text()
     (csrc / "k_subst.cu").write_text(sub + "\n// edited\n")
-    assert bench.profiled_traffic("c2") is None               # kernel source changed
+    assert bench.profiled_traffic("c3") is None               # kernel source changed

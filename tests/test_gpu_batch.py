@@ -196,6 +196,9 @@ def test_batched_entry_point_uses_the_plan(dev, uneven):
     outs, infos = stfdm.st_fdm_solve_batched(hs, Fs, P0, precision="mixed")
     for h, F, p0, o, ref in zip(hs, Fs, P0, outs, refs):
         single, _ = stfdm.st_fdm_solve(h, F, p0, precision="mixed")
+        # two different GMRES iterates, each with a relative residual <= 1e-12: their errors lie
+        # along the operator's small singular directions and can reach cond(K) times the residual
+        # (about 1e3 here), so they agree to about 1e-9 in the worst case; 1e-10 is the bound
         assert rel(o.cpu().numpy(), single.cpu().numpy()) <= 1e-10
         assert rel(o.cpu().numpy(), ref) <= 1e-9
 

@@ -19,12 +19,22 @@ pytestmark = pytest.mark.gpu
 def test_c3_mixed_p2_packets():
     """384x384 squares P1 (146,689 nodes, b = 384), P2 time on 512 elements (n_t = 1024), T = 2,
     psi0 = four seeded packets, f = 0: 150,209,536 unknowns.  The factors (463 GB) do not fit, so
-    every FP32 application refactorises.  Checks at this size: the oracle's FP64 residual of the
-    mixed solution meets the 1e-10 target, and sampled spatial solves agree with SuperLU."""
+    the systems whose factors are not kept refactorise at every FP32 application.  Checks at this
+    size:
+      * the oracle's FP64 residual of the mixed solution meets the 1e-10 target;
+      * its relative error against two FP64 references, each with its own oracle residual stated:
+        the GPU FP64 FDM and the oracle's CPU FP64 FDM (SuperLU per eigen-index on the host pool)
+        with one FP64 refinement sweep.  The plain FP64 FDM carries the rounding of X_t, about
+        kappa_2(X_t) eps ~ 1e-11..1e-10 in the residual, and a residual maps to an error up to
+        cond(K) larger (a GMRES iterate's error lies along the operator's small singular
+        directions), so the 1e-9 bar is asserted against the reference whose residual is below
+        the mixed solution's -- the refined CPU FDM -- and the others are reported;
+      * sampled spatial solves agree with SuperLU."""
     if not torch.cuda.is_available():
         pytest.skip("no CUDA device")
     import time
 
+    from oracle import cpu_fdm
     from paper_2504_07269_gb300 import build, stfdm
 
     build.build()
@@ -40,21 +50,41 @@ def test_c3_mixed_p2_packets():
     p0 = torch.from_numpy(psi0).to(dev)
     torch.cuda.synchronize()
     t2 = time.perf_counter()
-    # the restart length follows the free memory; allow for slower restarted convergence
     psi, info = stfdm.st_fdm_solve(h, F, p0, precision="mixed", tol=1e-10, max_sweeps=80)
     torch.cuda.synchronize()
     t3 = time.perf_counter()
     print(f"c3: setup {t1 - t0:.1f} s (kappa_X {h.kappa:.2e}), mixed solve {t3 - t2:.1f} s = "
-          f"{pr.unknowns / (t3 - t2):.3e} unknowns/s, sweeps {info['sweeps']}, factors kept {info['factors_kept']}, "
-          f"residual {info['rel_residual']:.2e}")
+          f"{pr.unknowns / (t3 - t2):.3e} unknowns/s, sweeps {info['sweeps']}, restart {info['restart']}, "
+          f"kept systems {info['kept_systems']}, residual {info['rel_residual']:.2e}")
     M_t, B_t, m_t, _ = fe_time.assemble_time(pr.p_t, pr.t_nodes)
     M_x, A_x = fe_space.assemble_space(pr.n)
     U = psi.cpu().numpy()
+    del psi
     Ft = -np.outer(m_t, A_x @ psi0)
     _, r = solve.residual(M_t, B_t, M_x, A_x, U - psi0[None, :], Ft)
-    print(f"c3 oracle residual {r:.2e}")
+    print(f"c3 mixed: oracle residual {r:.2e}")
     assert r <= 1e-10
-    del psi, U
+    # reference 1: the GPU FP64 FDM on the same inputs
+    psi64, _ = stfdm.st_fdm_solve(h, F, p0, precision="fp64")
+    U64 = psi64.cpu().numpy()
+    del psi64, F
+    torch.cuda.empty_cache()
+    _, r64 = solve.residual(M_t, B_t, M_x, A_x, U64 - psi0[None, :], Ft)
+    e64 = np.linalg.norm(U - U64) / np.linalg.norm(U64)
+    del U64
+    # reference 2: the oracle's CPU FP64 FDM, plain and with one FP64 refinement sweep
+    rep = {}
+    t4 = time.perf_counter()
+    Ucpu = cpu_fdm.cpu_fdm_refined(pr.n, pr.p_t, pr.t_nodes, np.zeros_like(U), psi0, sweeps=1, report=rep)
+    t5 = time.perf_counter()
+    ecpu = np.linalg.norm(U - rep["unrefined"]) / np.linalg.norm(rep["unrefined"])
+    eref = np.linalg.norm(U - Ucpu) / np.linalg.norm(Ucpu)
+    print(f"c3 mixed vs GPU FP64 FDM {e64:.2e} (its oracle residual {r64:.2e}); vs CPU FP64 FDM {ecpu:.2e} "
+          f"(its residual {rep['residuals'][0]:.2e}); vs refined CPU FDM {eref:.2e} (its residual "
+          f"{rep['residuals'][-1]:.2e}; {t5 - t4:.0f} s on the host)")
+    assert rep["residuals"][-1] < r           # the tight reference
+    assert eref <= 1e-9
+    del Ucpu, rep, U
     # sampled spatial solves at this size (b = 384)
     _, s, _, _ = stfdm.st_time_decompose(h.time)
     G = synth.cn01((h.n_t, h.n_x), seed=78)
@@ -76,10 +106,11 @@ def test_c4_adjoint_gradient_vs_finite_differences():
     """J(f) = 1/2 ||psi_h(f) - psi_target||^2_W + alpha/2 ||f||^2_W, W = M_t (x) M_x, F = W f,
     alpha = 1e-3, target and psi0 seeded packets (128x128 squares, P1 time N_t = 256, T = 1).
     The gradient W K^{-H} W e + alpha W f (one adjoint solve) against central differences of J
-    (two FP64 forward solves each) along 20 seeded complex directions (|d| = |f|).  J is quadratic
-    in f, so the difference quotient has no truncation error for any step: at h = 1e-3 it checks
-    the gradient to 1e-6; at h = 1e-6 the forward solves' rounding (about 1e-11 relative) is
-    amplified by 1/h, which bounds the agreement near 1e-5 (measured and reported)."""
+    (two forward solves each) along 20 seeded complex directions (|d| = |f|).  J is quadratic in f,
+    so the difference quotient has no truncation error for any step; its only error is the forward
+    solves' rounding divided by h.  At h = 1e-3 the plain FP64 FDM (rounding about 1e-11 relative,
+    kappa_2(X_t) eps) checks the gradient to 1e-6; at the configured h = 1e-6 the forward solves
+    are refined to a 1e-13 FP64 residual, and the bar is 1e-6 on all 20 directions."""
     if not torch.cuda.is_available():
         pytest.skip("no CUDA device")
     from paper_2504_07269_gb300 import build, stfdm
@@ -103,11 +134,13 @@ def test_c4_adjoint_gradient_vs_finite_differences():
         return np.vdot(a, W(b))
 
     def forward(f, precision="fp64"):
-        psi, _ = stfdm.st_fdm_solve(h, torch.from_numpy(W(f)).to(dev), p0, precision=precision)
+        # mixed: refined to a 1e-13 FP64 residual, whose rounding (divided by h) stays below the bar
+        psi, _ = stfdm.st_fdm_solve(h, torch.from_numpy(W(f)).to(dev), p0, precision=precision,
+                                    tol=1e-13 if precision == "mixed" else 0.0, max_sweeps=60)
         return psi.cpu().numpy()
 
-    def J(f):
-        e = forward(f) - target
+    def J(f, precision="fp64"):
+        e = forward(f, precision) - target
         return 0.5 * wdot(e, e).real + 0.5 * alpha * wdot(f, f).real
 
     f = synth.cn01((h.n_t, h.n_x), seed=pr.seed + 2)
@@ -118,14 +151,14 @@ def test_c4_adjoint_gradient_vs_finite_differences():
     for i in range(20):
         d = synth.cn01(f.shape, seed=1000 + i)
         dirs.append(d * (np.linalg.norm(f) / np.linalg.norm(d)))
-    for hstep, ndir, bar in ((1e-3, 20, 1e-6), (1e-6, 5, 1e-4)):
+    for hstep, ndir, bar, prec in ((1e-3, 20, 1e-6, "fp64"), (1e-6, 20, 1e-6, "mixed")):
         gaps = []
         for d in dirs[:ndir]:
-            fd = (J(f + hstep * d) - J(f - hstep * d)) / (2 * hstep)
+            fd = (J(f + hstep * d, prec) - J(f - hstep * d, prec)) / (2 * hstep)
             ad = np.vdot(g, d).real
             gaps.append(abs(fd - ad) / abs(ad))
-        print(f"c4 adjoint gradient vs central differences, h = {hstep:g} ({ndir} directions): relative gaps "
-              f"max {max(gaps):.2e}, median {np.median(gaps):.2e}")
+        print(f"c4 adjoint gradient vs central differences, h = {hstep:g} ({ndir} directions, forward solves "
+              f"{prec}): relative gaps max {max(gaps):.2e}, median {np.median(gaps):.2e}")
         assert max(gaps) <= bar
     # the mixed-precision adjoint (FP32 FDM refined by FP64 GMRES) against the FP64 adjoint
     try:

@@ -57,9 +57,10 @@ def test_fullsize_mixed_residual_and_vs_fp64(c2):
     print(f"c2 mixed vs fp64: {err:.2e}")
     assert err <= 1e-9
     _, r64 = solve.residual(c2["M_t"], c2["B_t"], c2["M_x"], c2["A_x"], U64 - c2["psi0"][None, :], Ft)
-    # the direct FP64 FDM carries the rounding of X_t: residual ~ kappa_2(X_t) eps (2.4e-10 measured)
+    # the direct FP64 FDM carries the rounding of X_t: its residual is far above the FP64 floor, of
+    # order kappa_2(X_t) eps sqrt(n_t) (2.4e-10 measured); the bound allows about 3x that
     print(f"c2 fp64 FDM oracle residual {r64:.2e} (kappa_2(X_t) eps = {h.kappa * 2.2e-16:.1e})")
-    assert r64 <= 1e4 * h.kappa * 2.2e-16
+    assert r64 <= 8e-10
     # discretisation check: the solution is close to the manufactured psi
     x1, x2 = synth.interior_coords(c2["pr"].n)
     ex = synth.psi_c1(x1[None, :], x2[None, :], c2["times"][:, None])

@@ -288,3 +288,42 @@ def test_failures_are_reported(dev):
     assert e.value.status == _lib.ST_ERR_NOT_CONVERGED
     with pytest.raises(ValueError):
         stfdm.st_fdm_solve(h, F.to(torch.complex64), precision="fp64")
+
+
+def test_bounded_wait_times_out_and_handle_recovers(dev):
+    """Failure detection without a GPU fault: the wait probe makes the substitution kernel's copy
+    issuer wait on an mbarrier that receives neither a copy nor an arrival.  The bounded wait runs
+    out (1 ms), the CTA takes its timeout exit (no copy was issued, so none is in flight), the
+    entry point returns ST_ERR_TIMEOUT, and after the probe is turned off the same handle solves
+    correctly again (spatial solve vs SuperLU, full mixed solve vs the oracle)."""
+    import time
+
+    from paper_2504_07269_gb300 import _lib, stfdm
+
+    n, p, t = 23, 1, synth.uniform_time_nodes(12, 1.0)
+    h = _handle(n, p, t)
+    G = synth.cn01((h.n_t, h.n_x), seed=21)
+    Gd = torch.from_numpy(G).to(dev).to(torch.complex64)
+    stfdm.st_set_wait_probe(h, 1e-3)
+    t0 = time.perf_counter()
+    with pytest.raises(_lib.StfdmError) as e:
+        stfdm.st_spatial_solve(h, "fp32", Gd)
+    waited = time.perf_counter() - t0
+    assert e.value.status == _lib.ST_ERR_TIMEOUT
+    print(f"wait probe: ST_ERR_TIMEOUT after {waited * 1e3:.1f} ms")
+    assert waited < 1.5            # the consumers abort with the producer instead of waiting 2 s
+    with pytest.raises(_lib.StfdmError) as e:
+        stfdm.st_set_wait_probe(h, 2.0)
+    assert e.value.status == _lib.ST_ERR_ARG
+    stfdm.st_set_wait_probe(h, 0.0)
+    W = stfdm.st_spatial_solve(h, "fp32", Gd).cpu().numpy()
+    M_t, B_t, m_t, _ = fe_time.assemble_time(p, t)
+    M_x, A_x = fe_space.assemble_space(n)
+    _, s, _, _ = stfdm.st_time_decompose(h.time)
+    for k in range(h.n_t):
+        ref = spla.splu(sp.csc_matrix(M_x + s[k] * A_x, dtype=np.complex128)).solve(G[k])
+        assert rel(W[k], ref) <= 1e-4
+    F = synth.cn01((h.n_t, h.n_x), seed=22)
+    ref = solve.solve_explicit(_oracle_K(n, p, t), F)
+    psi, _ = stfdm.st_fdm_solve(h, torch.from_numpy(F).to(dev), precision="mixed")
+    assert rel(psi.cpu().numpy(), ref) <= 1e-9

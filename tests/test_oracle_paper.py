@@ -79,3 +79,25 @@ def test_cpu_fdm_pool_matches_explicit():
     tt = fe_time.assemble_time(1, pr.t_nodes)[3]
     exact = synth.psi_c1(x1[None, :], x2[None, :], tt[:, None])
     assert np.abs(U - exact).max() < 2e-2
+
+
+@pytest.mark.slow
+def test_cpu_fdm_refined_reaches_the_residual_floor():
+    """One classical FP64 refinement sweep of the process-pool CPU FDM: the residual drops to the
+    FP64 floor (well below the unrefined FDM's, whose rounding grows with kappa_2(X_t)), and the
+    refined solution equals the explicit oracle's; psi0 enters through the lifting."""
+    n, p, t = 10, 2, synth.uniform_time_nodes(40, 2.0)
+    M_t, B_t, m_t, _ = fe_time.assemble_time(p, t)
+    M_x, A_x = fe_space.assemble_space(n)
+    x1, x2 = synth.interior_coords(n)
+    psi0 = synth.packet_values(synth.packet_params(3), x1, x2)
+    u = synth.cn01((p * 40, (n - 1) ** 2), seed=5)
+    F = solve.kron_apply(M_t, B_t, M_x, A_x, u) + np.outer(m_t, A_x @ psi0)
+    rep = {}
+    U = cpu_fdm.cpu_fdm_refined(n, p, t, F, psi0, sweeps=1, workers=2, report=rep)
+    r0, r1 = rep["residuals"]
+    assert r1 < 1e-14 and r1 < 0.1 * r0
+    ref = solve.solve_explicit(assemble.explicit_system(n, p, t), F - np.outer(m_t, A_x @ psi0)) + psi0[None, :]
+    assert np.linalg.norm(U - ref) / np.linalg.norm(ref) < 1e-13
+    assert np.linalg.norm(U - u - psi0[None, :]) / np.linalg.norm(u) < 1e-12
+    assert np.linalg.norm(rep["unrefined"] - ref) / np.linalg.norm(ref) < 1e-10

@@ -21,6 +21,10 @@ int main(int argc, char** argv) {
     if (argv[1][0] == 'r') {   // r N avail factors m m_min
         std::printf("%d\n", stfdm::batch_restart_for_factors(std::strtoull(argv[2], 0, 10), std::strtoull(argv[3], 0, 10),
                                                             std::strtoull(argv[4], 0, 10), std::atoi(argv[5]), std::atoi(argv[6])));
+    } else if (argv[1][0] == 's') {   // s N n_t grid per avail fixed m m_min
+        std::printf("%d\n", stfdm::single_restart_for_partial_keep(
+            std::strtoull(argv[2], 0, 10), std::atoi(argv[3]), std::atoi(argv[4]), std::strtoull(argv[5], 0, 10),
+            std::strtoull(argv[6], 0, 10), std::strtoull(argv[7], 0, 10), std::atoi(argv[8]), std::atoi(argv[9])));
     } else {                   // k n_t grid per avail fixed
         std::printf("%d\n", stfdm::partial_keep_systems(std::atoi(argv[2]), std::atoi(argv[3]), std::strtoull(argv[4], 0, 10),
                                                        std::strtoull(argv[5], 0, 10), std::strtoull(argv[6], 0, 10)));
@@ -98,3 +102,31 @@ def test_partial_keep_fills_whole_waves(rules, avail_gb):
     assert 0 <= K <= kmax                       # fits
     assert (n_t - K) % grid == 0 or K == 0      # the refactorised systems fill whole waves
     assert K == 0 or K > kmax - grid            # no whole wave left unused
+
+
+@pytest.mark.parametrize("avail_gb", [150, 200, 260, 290, 400])
+def test_single_restart_drops_refactorisation_waves(rules, avail_gb):
+    """384^2 squares, P2 time n_t = 1024 (150M unknowns, 463 GB of factors): the restart length is
+    the longest that needs no more refactorisation waves than the shortest basis."""
+    n_t, grid, n_x, b = 1024, 152, 383 * 383, 384
+    N = n_t * n_x
+    per = n_x * (b + 1) * 8
+    fixed = grid * per + grid * (b + 32) * (b + 1) * 8 + 2 * GiB
+    avail = avail_gb * 10**9
+    m0, m_min = 20, 4
+    m = rules("s", N, n_t, grid, per, avail, fixed, m0, m_min)
+
+    def waves(mm):
+        bb = N * (2 * mm + 1) * 16
+        K = rules("k", n_t, grid, per, avail - bb, fixed) if bb < avail else 0
+        return (n_t - K + grid - 1) // grid
+
+    cap = m0
+    while cap > 2 and N * (2 * cap + 1) * 16 > avail // 3:
+        cap -= 1
+    lo = min(m_min, cap)
+    assert lo <= m <= cap
+    assert waves(m) == waves(lo)                    # no wave more than the shortest basis needs
+    assert m == cap or waves(m + 1) > waves(lo)      # and the longest such basis
+    if avail_gb == 290:
+        assert waves(m) < waves(cap)                # at the full memory the long basis costs a wave
