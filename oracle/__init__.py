@@ -15,6 +15,8 @@ definitions, slow and obviously correct:
   fe_time      M_t, B_t, m_t from their integral definitions, eq. (matrix_t),
                P1 and P2 Lagrange elements, t0 DOF removed (Section 3).
   fe_space     structured triangulation, M_x, A_x from eq. (matrix_x), P1.
+  fe_mesh      M_x, A_x of eq. (matrix_x) on any triangle (d = 2) or tetrahedron
+               (d = 3) mesh, Lagrange P1 and P2, Dirichlet DOFs removed.
   assemble     explicit space-time prism assembly of K = iB_t (x) M_x + M_t (x) A_x
                (eq. LGS) straight from the sesquilinear form a(u,v) of eq.
                (VF_inhomogen) on each prism; load vector and lifting of

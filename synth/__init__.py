@@ -21,7 +21,8 @@ __all__ = [
     "uniform_time_nodes", "graded_time_nodes", "interior_coords", "cn01",
     "PacketParams", "packet_params", "packet_values",
     "psi_c1", "f_c1", "psi0_c1", "psi_paper", "f_paper",
-    "Problem", "config_problem", "batch_problems",
+    "Problem", "config_problem", "batch_problems", "square_delaunay_mesh", "cube_tet_mesh",
+    "packet_values_nd",
 ]
 
 
@@ -52,6 +53,69 @@ def interior_coords(n: int, Lx: float = 1.0, Ly: float = 1.0):
     x1 = np.tile(i * (Lx / n), m)
     x2 = np.repeat(i * (Ly / n), m)
     return x1, x2
+
+
+def square_delaunay_mesh(n: int, jitter: float = 0.3, seed: int = 0, L: float = 1.0):
+    """An unstructured triangulation of (0,L)^2: the Delaunay triangulation of the (n+1)^2 grid
+    points with every interior point moved by up to `jitter` h in each coordinate (h = L/n,
+    seeded), boundary points fixed.  Returns (coords[V, 2], triangles[C, 3]) with
+    counter-clockwise triangles."""
+    from scipy.spatial import Delaunay
+
+    rng = np.random.Generator(np.random.PCG64(seed))
+    h = L / n
+    i, j = np.meshgrid(np.arange(n + 1), np.arange(n + 1), indexing="xy")
+    xy = np.stack([i.ravel() * h, j.ravel() * h], axis=1)
+    inner = (i.ravel() > 0) & (i.ravel() < n) & (j.ravel() > 0) & (j.ravel() < n)
+    xy[inner] += rng.uniform(-jitter * h, jitter * h, size=(int(inner.sum()), 2))
+    tri = Delaunay(xy).simplices.astype(np.int64)
+    a, b, c = xy[tri[:, 0]], xy[tri[:, 1]], xy[tri[:, 2]]
+    cross = (b[:, 0] - a[:, 0]) * (c[:, 1] - a[:, 1]) - (b[:, 1] - a[:, 1]) * (c[:, 0] - a[:, 0])
+    tri[cross < 0] = tri[cross < 0][:, [0, 2, 1]]
+    return xy, tri
+
+
+def cube_tet_mesh(n: int, jitter: float = 0.2, seed: int = 0, L: float = 1.0):
+    """A tetrahedral mesh of (0,L)^3: n^3 cubes, each split into the 6 tetrahedra around its main
+    diagonal (a conforming split), interior vertices moved by up to `jitter` h in each coordinate
+    (seeded).  Returns (coords[V, 3], tets[C, 4])."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    h = L / n
+    g = np.arange(n + 1)
+    I, J, K = np.meshgrid(g, g, g, indexing="ij")
+    idx = lambda a, b, c: (a * (n + 1) + b) * (n + 1) + c   # noqa: E731
+    xyz = np.stack([I.ravel(), J.ravel(), K.ravel()], axis=1).astype(np.float64) * h
+    inner = np.all((np.stack([I.ravel(), J.ravel(), K.ravel()], axis=1) > 0) &
+                   (np.stack([I.ravel(), J.ravel(), K.ravel()], axis=1) < n), axis=1)
+    xyz[inner] += rng.uniform(-jitter * h, jitter * h, size=(int(inner.sum()), 3))
+    c0 = np.stack(np.meshgrid(np.arange(n), np.arange(n), np.arange(n), indexing="ij"), axis=-1).reshape(-1, 3)
+    # the 6 monotone lattice paths from corner (0,0,0) to (1,1,1)
+    paths = [(0, 1, 2), (0, 2, 1), (1, 0, 2), (1, 2, 0), (2, 0, 1), (2, 1, 0)]
+    tets = []
+    for pth in paths:
+        v = [c0.copy()]
+        cur = c0.copy()
+        for ax in pth:
+            cur = cur.copy()
+            cur[:, ax] += 1
+            v.append(cur)
+        tets.append(np.stack([idx(q[:, 0], q[:, 1], q[:, 2]) for q in v], axis=1))
+    return xyz, np.concatenate(tets, axis=0).astype(np.int64)
+
+
+def packet_values_nd(p: "PacketParams", x: np.ndarray) -> np.ndarray:
+    """Gaussian packets at points x (P, d), d = 2 or 3: the parameters' centres and momenta give
+    the first two components; a third coordinate is centred at 0.5 with zero momentum."""
+    d = x.shape[1]
+    out = np.zeros(x.shape[0], dtype=np.complex128)
+    for s, c, k in zip(p.sigma, p.centre, p.k):
+        cc = np.full(d, 0.5)
+        kk = np.zeros(d)
+        cc[:2] = c[:2]
+        kk[:2] = k[:2]
+        r2 = ((x - cc) ** 2).sum(axis=1)
+        out += np.exp(-r2 / (2 * s * s)) * np.exp(1j * (x @ kk))
+    return out
 
 
 # ---------------------------------------------------------------- random
