@@ -80,10 +80,16 @@ typedef struct st_time st_time;
 typedef struct st_space st_space;
 typedef struct st_fdm st_fdm;
 
+/* spatial solvers of step 3 (st_setup_opts.spatial_solver) */
+#define ST_SPATIAL_AUTO          0   /* banded for structured grids, multifrontal for meshes */
+#define ST_SPATIAL_BANDED        1   /* pivot-free banded LDL^T (structured grids only) */
+#define ST_SPATIAL_MULTIFRONTAL  2   /* pivot-free sparse-direct multifrontal LDL^T, nested dissection */
+
 typedef struct {
     double kappa_max;   /* reject X_t with kappa_2 above this; <= 0 selects 1e10 (Section 3: X_t must be regular) */
     int device;         /* CUDA device ordinal for the handle's device data; < 0 = the current device */
     int host_threads;   /* threads for the host FP64 setup; <= 0 = hardware concurrency */
+    int spatial_solver; /* ST_SPATIAL_*; 0 = automatic */
 } st_setup_opts;
 
 typedef struct {
@@ -126,7 +132,7 @@ typedef struct {
 const char* st_status_string(st_status s);
 const char* st_last_error_message(void);
 int st_abi_version(void);   /* returns STFDM_ABI_VERSION of the built library */
-#define STFDM_ABI_VERSION 5
+#define STFDM_ABI_VERSION 6
 
 /* ------------------------------------------------------------------ assembly (host) */
 /* Temporal matrices of eq. (matrix_t), Section 3.  p_t in {1, 2}: continuous piecewise
@@ -146,6 +152,34 @@ st_status st_time_get(const st_time* t, int* n_t, double* M_t, double* B_t, doub
 st_status st_assemble_space(int n_squares, double Lx, double Ly, st_space** out);
 /* coeffs[8] = {Mc, Mw(=Me), Ms(=Mn), Mdiag(SW/NE), Ac, Aw, As, Adiag}; m = n_squares - 1. */
 st_status st_space_get(const st_space* s, int* m, int* n_x, double* coeffs);
+
+/* Spatial matrices of eq. (matrix_x) on a general conforming simplicial mesh (the spaces S^p_hx of
+ * Section 2 for d = 2, 3): Lagrange P1 or P2 (p_x), triangles (dim = 2) or tetrahedra (dim = 3).
+ * coords: host doubles (n_vertices, dim) row-major; cells: host ints (n_cells, dim + 1), vertex
+ * indices (any orientation).  DOFs: the vertices in input order, then for P2 one per edge, the
+ * edges ordered by their (smaller vertex, larger vertex) pair; DOFs on a boundary facet (a facet of
+ * exactly one cell) are removed (Dirichlet), the interior DOFs keep this order (it is the order of
+ * every spatial index of the solver's arrays).  The integrals are exact (barycentric monomials).
+ * The handle works with every entry point except the structured-grid helpers (st_space_get,
+ * st_error_norms, st_load_quadrature, st_residual_noalloc) and batched plans; its spatial systems
+ * are solved by the multifrontal solver.  Errors: ST_ERR_ARG (dim, p_x, index out of range, a
+ * degenerate cell, a facet shared by more than two cells, no interior DOF), ST_ERR_OOM. */
+st_status st_assemble_mesh(int dim, int p_x, int n_vertices, const double* coords, int n_cells, const int* cells,
+                           st_space** out);
+/* The spatial matrices in CSR over the interior DOFs (one pattern for M_x and A_x, sorted columns;
+ * for a structured grid its 7-point stencils): rowptr[n_x + 1], col[nnz], M[nnz], A[nnz], and the
+ * interior DOFs' coordinates xyz[n_x * dim]; any output may be NULL (query sizes first). */
+st_status st_space_get_mesh(const st_space* s, int* dim, int* p_x, int* n_x, long long* nnz, int* rowptr, int* col,
+                            double* M, double* A, double* xyz);
+/* The sparse-direct solver's plan for a space (host only): nested dissection by coordinate bisection
+ * with leaves of at most `leaf` DOFs (<= 0: 64) and its multifrontal assembly tree.  Outputs (any may
+ * be NULL): fronts, launch levels, the largest front, factor entries per system, real flops of one
+ * factorisation (8 per complex multiply-add), perm[n_x] (elimination position -> DOF), per front
+ * its first pivot position, pivot count and update-row count, and the update rows of all fronts
+ * concatenated (elimination positions, ascending per front). */
+st_status st_space_mf_plan(const st_space* s, int leaf, int* n_fronts, int* n_levels, int* max_front,
+                           long long* factor_entries, double* flops, int* perm, int* front_first, int* front_np,
+                           int* front_nu, int* urows);
 
 /* Step 1 on the host, no device needed (Section 3, fast diagonalisation): X_t (unit 2-norm
  * columns), s (eigenvalues), Y_t = X_t^{-1} (i B_t)^{-1}, kappa_2(X_t).  X, Y: host

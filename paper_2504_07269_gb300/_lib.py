@@ -24,6 +24,10 @@ ST_ERR_NOT_CONVERGED = -6
 ST_ERR_TIMEOUT = -7
 ST_ERR_UNSUPPORTED = -8
 
+ST_SPATIAL_AUTO = 0
+ST_SPATIAL_BANDED = 1
+ST_SPATIAL_MULTIFRONTAL = 2
+
 ST_FP64 = 0
 ST_FP32 = 1
 ST_MIXED = 2
@@ -41,7 +45,7 @@ ST_XFORM_YT = 3
 
 
 class st_setup_opts(ctypes.Structure):
-    _fields_ = [("kappa_max", c_double), ("device", c_int), ("host_threads", c_int)]
+    _fields_ = [("kappa_max", c_double), ("device", c_int), ("host_threads", c_int), ("spatial_solver", c_int)]
 
 
 class st_solve_opts(ctypes.Structure):
@@ -106,6 +110,11 @@ SIGNATURES = {
     "st_load_quadrature": (c_int, [c_void_p, c_int, c_int, c_int, c_void_p, c_void_p]),
     "st_residual_noalloc": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]),
     "st_set_wait_probe": (c_int, [c_void_p, c_double]),
+    "st_assemble_mesh": (c_int, [c_int, c_int, c_int, c_void_p, c_int, c_void_p, c_void_p]),
+    "st_space_get_mesh": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p,
+                                  c_void_p, c_void_p]),
+    "st_space_mf_plan": (c_int, [c_void_p, c_int, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p,
+                                 c_void_p, c_void_p, c_void_p, c_void_p]),
     "st_destroy_time": (None, [c_void_p]),
     "st_destroy_space": (None, [c_void_p]),
     "st_destroy_fdm": (None, [c_void_p]),

@@ -144,6 +144,15 @@ void free_handle(st_fdm* h) {
     cudaFree(h->kry_small);
     for (int i = 0; i < 4; ++i) cudaFree(h->tc_A[i]);
     cudaFree(h->tc_bt);
+    cudaFree(h->csr_rowptr);
+    cudaFree(h->csr_col);
+    cudaFree(h->csr_M);
+    cudaFree(h->csr_A);
+    cudaFree(h->mf_fronts);
+    cudaFree(h->mf_ints);
+    cudaFree(h->mf_csrv);
+    cudaFree(h->mf_upd);
+    cudaFree(h->mf_uvec);
     delete h;
 }
 
@@ -231,6 +240,7 @@ const float2* shifts_of<float>(const st_fdm* h) { return h->s32; }
 // One wave of transient factors: grid = resident CTAs of the complex64 factor kernel, per = bytes
 // of one system's L and D, fixed = the wave's factors, its windows and a 2 GiB reserve.
 bool partial_keep_geometry(const st_fdm* h, int& grid, size_t& per, size_t& fixed) {
+    if (h->spatial == 1) return false;   // the sparse-direct factors are kept whole or refactorised
     const int n_t = h->tm.n_t, n = h->sm.n_x, b = h->sm.m + 1;
     const int nb = band_pick_nb<float>(b, h->smem_optin);
     if (nb == 0) return false;
@@ -243,6 +253,7 @@ bool partial_keep_geometry(const st_fdm* h, int& grid, size_t& per, size_t& fixe
 }
 
 int partial_keep_count(st_fdm* h) {
+    if (h->spatial == 1) return 0;
     int grid = 0;
     size_t per = 0, fixed = 0;
     if (!partial_keep_geometry(h, grid, per, fixed)) return 0;
@@ -253,12 +264,129 @@ int partial_keep_count(st_fdm* h) {
     return partial_keep_systems(h->tm.n_t, grid, per, avail, fixed);
 }
 
+bool mf_factors_fit(st_fdm* h, size_t elem);
+
 bool factors_fit(st_fdm* h, size_t elem) {
+    if (h->spatial == 1) return mf_factors_fit(h, elem);
     size_t freeb = 0, total = 0;
     if (cudaMemGetInfo(&freeb, &total) != cudaSuccess) return false;
     const size_t need = (size_t)h->tm.n_t * h->sm.n_x * (size_t)(h->sm.m + 1 + 1) * elem;
     size_t have = h->ws_L_bytes + h->ws_D_bytes;
     return need <= (size_t)(0.85 * (double)(freeb + have));
+}
+
+// ------------------------------------------------------------------ sparse-direct spatial solves
+// Multifrontal factor-and-solve of all n_t systems (general meshes, or structured grids set up
+// with ST_SPATIAL_MULTIFRONTAL).  mode 0: factors transient, systems in chunks; 1: factor all
+// systems into kept storage, then solve; 2: solve with the kept factors.  The update matrices and
+// vectors live only for a chunk of systems.
+bool mf_factors_fit(st_fdm* h, size_t elem) {
+    size_t freeb = 0, total = 0;
+    if (cudaMemGetInfo(&freeb, &total) != cudaSuccess) return false;
+    const size_t need = (size_t)h->tm.n_t * (size_t)h->mf.factor_entries * elem;
+    const size_t have = h->ws_L_bytes + h->mf_upd_bytes + h->mf_uvec_bytes;
+    return need <= (size_t)(0.8 * (double)(freeb + have));
+}
+
+template <typename T>
+st_status mf_run(st_fdm* h, C<T>* G, int mode, cudaStream_t st) {
+    const MfPlan& P = h->mf;
+    const int n_t = h->tm.n_t;
+    const size_t esz = sizeof(C<T>);
+    const int H = (int)P.level_ptr.size() - 1;
+    if (mode == 2 && (!h->factors_valid || h->factors_prec != (int)esz))
+        return fail(ST_ERR_ARG, "spatial solve: no stored factors");
+    size_t freeb = 0, total = 0;
+    CUDA_TRY(cudaMemGetInfo(&freeb, &total));
+    size_t avail = freeb + h->mf_upd_bytes + h->mf_uvec_bytes + (mode == 2 ? 0 : h->ws_L_bytes);
+    if (mode == 1) {
+        const size_t kept = (size_t)n_t * P.factor_entries * esz;
+        if (kept > avail) return fail(ST_ERR_OOM, "spatial solve: kept factors do not fit");
+        avail -= kept;
+    }
+    // systems per chunk: transient storage within 40% of what is available
+    size_t per = (size_t)(P.update_entries + P.uvec_entries) * esz;
+    if (mode == 0) per += (size_t)P.factor_entries * esz;
+    if (mode == 2) per = (size_t)P.uvec_entries * esz;
+    long long kc = per ? (long long)((double)avail * 0.4 / (double)per) : n_t;
+    kc = std::max(1LL, std::min<long long>(kc, std::min(n_t, 65535)));
+    st_status s = ST_OK;
+    if (mode != 2) {
+        s = grow(h->mf_upd, h->mf_upd_bytes, std::max<size_t>(16, (size_t)kc * P.update_entries * esz), "update matrices");
+        if (s != ST_OK) return s;
+    }
+    s = grow(h->mf_uvec, h->mf_uvec_bytes, std::max<size_t>(16, (size_t)kc * P.uvec_entries * esz), "update vectors");
+    if (s != ST_OK) return s;
+    if (mode == 1) {
+        h->factors_valid = 0;
+        s = resize(h->ws_L, h->ws_L_bytes, (size_t)n_t * P.factor_entries * esz, "kept factors");
+    } else if (mode == 0) {
+        h->factors_valid = 0;
+        s = grow(h->ws_L, h->ws_L_bytes, (size_t)kc * P.factor_entries * esz, "factors");
+    }
+    if (s != ST_OK) return s;
+    MfArgs<T> a;
+    a.fronts = h->mf_fronts;
+    a.level_fronts = h->mf_level;
+    a.lvl_off = 0;
+    a.urows = h->mf_urows;
+    a.relpos = h->mf_relpos;
+    a.children = h->mf_children;
+    a.orig_r = h->mf_orig_r;
+    a.orig_c = h->mf_orig_c;
+    a.orig_k = h->mf_orig_k;
+    a.perm = h->mf_perm;
+    if (h->sm.kind == 1) {
+        a.Mv = h->csr_M;
+        a.Av = h->csr_A;
+    } else {
+        a.Mv = h->mf_csrv;
+        a.Av = h->mf_csrv + h->mf_csrv_nnz;
+    }
+    a.shifts = shifts_of<T>(h);
+    a.fac = reinterpret_cast<C<T>*>(h->ws_L);
+    a.fac_stride = P.factor_entries;
+    a.fac_keep = (mode == 0) ? 0 : 1;
+    a.upd = reinterpret_cast<C<T>*>(h->mf_upd);
+    a.upd_stride = P.update_entries;
+    a.uvec = reinterpret_cast<C<T>*>(h->mf_uvec);
+    a.uvec_stride = P.uvec_entries;
+    a.rhs = G;
+    a.n = h->sm.n_x;
+    a.status = h->ws_status;
+    auto levels = [&](int k0, int cnt, int what) -> cudaError_t {
+        a.k0 = k0;
+        if (what == 0) {
+            for (int l = 0; l < H; ++l) {
+                cudaError_t e = mf_factor_launch<T>(a, P.level_ptr[l], P.level_ptr[l + 1] - P.level_ptr[l], cnt, st);
+                if (e != cudaSuccess) return e;
+            }
+        } else if (what == 1) {
+            for (int l = 0; l < H; ++l) {
+                cudaError_t e = mf_solve_launch<T>(a, P.level_ptr[l], P.level_ptr[l + 1] - P.level_ptr[l], cnt,
+                                                   P.max_front, true, st);
+                if (e != cudaSuccess) return e;
+            }
+        } else {
+            for (int l = H - 1; l >= 0; --l) {
+                cudaError_t e = mf_solve_launch<T>(a, P.level_ptr[l], P.level_ptr[l + 1] - P.level_ptr[l], cnt,
+                                                   P.max_front, false, st);
+                if (e != cudaSuccess) return e;
+            }
+        }
+        return cudaSuccess;
+    };
+    for (int k0 = 0; k0 < n_t; k0 += (int)kc) {
+        const int cnt = (int)std::min<long long>(kc, n_t - k0);
+        if (mode != 2) CUDA_TRY(levels(k0, cnt, 0));
+        CUDA_TRY(levels(k0, cnt, 1));
+        CUDA_TRY(levels(k0, cnt, 2));
+    }
+    if (mode == 1) {
+        h->factors_valid = 1;
+        h->factors_prec = (int)esz;
+    }
+    return ST_OK;
 }
 
 // mode: 0 = factor and solve (factors transient, in chunks of systems), 1 = factor, keep all
@@ -268,6 +396,10 @@ bool factors_fit(st_fdm* h, size_t elem) {
 //       (substitutions for the kept systems)
 template <typename T>
 st_status band_run(st_fdm* h, C<T>* G, int mode, cudaStream_t st) {
+    if (h->spatial == 1) {
+        if (mode == 3 || mode == 4) return fail(ST_ERR_ARG, "spatial solve: partial keep is for banded factors");
+        return mf_run<T>(h, G, mode, st);
+    }
     const SpaceMats& sm = h->sm;
     const int n = sm.n_x, b = sm.m + 1, n_t = h->tm.n_t;
     const int nb = band_pick_nb<T>(b, h->smem_optin);
@@ -606,7 +738,8 @@ st_status solve_mixed_gmres(st_fdm* h, bool adjoint, const void* F, const void* 
         cudaMemGetInfo(&freeb, &total);
         size_t avail = freeb + h->ws_kry_bytes;
         if (keep) {
-            const size_t fac = (size_t)n_t * n_x * (size_t)(h->sm.m + 2) * sizeof(float2);
+            const size_t fac = h->spatial == 1 ? (size_t)n_t * (size_t)h->mf.factor_entries * sizeof(float2)
+                                               : (size_t)n_t * n_x * (size_t)(h->sm.m + 2) * sizeof(float2);
             avail = avail > fac + h->ws_L_bytes ? avail - (fac > h->ws_L_bytes ? fac - h->ws_L_bytes : 0) : 0;
         }
         int grid = 0;
@@ -803,6 +936,77 @@ void fill_info_common(const st_fdm* h, st_solve_info* info, int precision) {
 
 }  // namespace
 
+// Spatial side of a handle: the device CSR of a general mesh, and the multifrontal plan when the
+// sparse-direct solver is used (general meshes always; structured grids on request).
+st_status setup_spatial(st_fdm* h, int choice) {
+    if (choice < 0 || choice > ST_SPATIAL_MULTIFRONTAL) return fail(ST_ERR_ARG, "st_fdm_setup: unknown spatial solver");
+    if (h->sm.kind == 1 && choice == ST_SPATIAL_BANDED)
+        return fail(ST_ERR_UNSUPPORTED, "st_fdm_setup: the banded spatial solver needs a structured grid");
+    st_status s = ST_OK;
+    if (h->sm.kind == 1) {
+        const MeshSpace& ms = h->sm.mesh;
+        s = upload(&h->csr_rowptr, ms.rowptr.data(), ms.rowptr.size() * sizeof(int), "CSR rows");
+        if (s == ST_OK) s = upload(&h->csr_col, ms.col.data(), ms.col.size() * sizeof(int), "CSR columns");
+        if (s == ST_OK) s = upload(&h->csr_M, ms.Mv.data(), ms.Mv.size() * sizeof(double), "CSR M_x");
+        if (s == ST_OK) s = upload(&h->csr_A, ms.Av.data(), ms.Av.size() * sizeof(double), "CSR A_x");
+        if (s != ST_OK) return s;
+        h->sm.d_rowptr = h->csr_rowptr;
+        h->sm.d_col = h->csr_col;
+        h->sm.d_M = h->csr_M;
+        h->sm.d_A = h->csr_A;
+    }
+    h->spatial = (h->sm.kind == 1 || choice == ST_SPATIAL_MULTIFRONTAL) ? 1 : 0;
+    if (!h->spatial) return ST_OK;
+    MeshSpace tmp;
+    const MeshSpace* ms = &h->sm.mesh;
+    if (h->sm.kind == 0) {
+        structured_as_mesh(h->sm, tmp);
+        ms = &tmp;
+        std::vector<double> v(ms->Mv);
+        v.insert(v.end(), ms->Av.begin(), ms->Av.end());
+        h->mf_csrv_nnz = (long long)ms->Mv.size();
+        s = upload(&h->mf_csrv, v.data(), v.size() * sizeof(double), "plan CSR values");
+        if (s != ST_OK) return s;
+    }
+    try {
+        s = build_mf_plan(*ms, 64, h->mf);
+    } catch (const std::bad_alloc&) {
+        return fail(ST_ERR_OOM, "st_fdm_setup: multifrontal plan (host)");
+    }
+    if (s != ST_OK) return s;
+    const MfPlan& P = h->mf;
+    if ((size_t)P.max_front * sizeof(double2) > h->smem_optin)
+        return fail(ST_ERR_UNSUPPORTED, "st_fdm_setup: a front of the sparse-direct solver exceeds shared memory");
+    std::vector<MfFrontDev> fd(P.fronts.size());
+    for (size_t i = 0; i < P.fronts.size(); ++i) {
+        const MfFront& f = P.fronts[i];
+        fd[i] = MfFrontDev{f.first, f.np, f.nu, f.parent, f.foff, f.uoff, f.uvoff,
+                           f.urows_off, f.relpos_off, f.orig_off, f.orig_cnt, f.child_off, f.child_cnt};
+    }
+    s = upload(&h->mf_fronts, fd.data(), fd.size() * sizeof(MfFrontDev), "plan fronts");
+    if (s != ST_OK) return s;
+    const std::vector<int>* parts[8] = {&P.perm, &P.urows, &P.relpos, &P.children, &P.orig_r, &P.orig_c, &P.orig_k,
+                                        &P.level_fronts};
+    std::vector<int> all;
+    size_t offs[8];
+    for (int i = 0; i < 8; ++i) {
+        offs[i] = all.size();
+        all.insert(all.end(), parts[i]->begin(), parts[i]->end());
+    }
+    all.push_back(0);
+    s = upload(&h->mf_ints, all.data(), all.size() * sizeof(int), "plan indices");
+    if (s != ST_OK) return s;
+    h->mf_perm = h->mf_ints + offs[0];
+    h->mf_urows = h->mf_ints + offs[1];
+    h->mf_relpos = h->mf_ints + offs[2];
+    h->mf_children = h->mf_ints + offs[3];
+    h->mf_orig_r = h->mf_ints + offs[4];
+    h->mf_orig_c = h->mf_ints + offs[5];
+    h->mf_orig_k = h->mf_ints + offs[6];
+    h->mf_level = h->mf_ints + offs[7];
+    return ST_OK;
+}
+
 // ==================================================================== setup
 extern "C" st_status st_fdm_setup(const st_time* t, const st_space* sp, const st_setup_opts* opts, st_fdm** out) {
     if (!out) return fail(ST_ERR_ARG, "st_fdm_setup: out is NULL");
@@ -923,6 +1127,7 @@ extern "C" st_status st_fdm_setup(const st_time* t, const st_space* sp, const st
         size_t parts = (size_t)residual_num_partials(n, h->sm.n_x);
         s = grow(*reinterpret_cast<void**>(&h->ws_red), h->ws_red_bytes, (8 + 2 * parts) * sizeof(double), "reduction");
     }
+    if (s == ST_OK) s = setup_spatial(h, o.spatial_solver);
     if (s == ST_OK) s = dev_alloc(reinterpret_cast<void**>(&h->ws_status), sizeof(int) * 4, "status");
     if (s == ST_OK && cudaMemset(h->ws_status, 0, sizeof(int) * 4) != cudaSuccess)
         s = fail(ST_ERR_CUDA, "st_fdm_setup: cudaMemset");

@@ -361,8 +361,11 @@ extern "C" st_status st_batch_create(st_fdm* const* hs, int count, const st_batc
     if (!out) return fail(ST_ERR_ARG, "st_batch_create: out is NULL");
     *out = nullptr;
     if (!hs || count < 1) return fail(ST_ERR_ARG, "st_batch_create: need at least one handle");
-    for (int i = 0; i < count; ++i)
+    for (int i = 0; i < count; ++i) {
         if (!hs[i]) return fail(ST_ERR_ARG, "st_batch_create: NULL handle");
+        if (hs[i]->spatial != 0)
+            return fail(ST_ERR_UNSUPPORTED, "st_batch_create: batched plans use the banded spatial solver (structured grids)");
+    }
     const int dev = hs[0]->device;
     for (int i = 1; i < count; ++i)
         if (hs[i]->device != dev) return fail(ST_ERR_ARG, "st_batch_create: handles on different devices");

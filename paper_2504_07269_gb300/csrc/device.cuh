@@ -172,6 +172,53 @@ struct BatchGm {
     int* pending;     // [1] problems not stopped at the start of the cycle
 };
 
+// multifrontal spatial solver (general meshes): device copy of a plan front
+struct MfFrontDev {
+    int first, np, nu, parent;
+    long long foff, uoff, uvoff;
+    int urows_off, relpos_off, orig_off, orig_cnt, child_off, child_cnt;
+};
+
+template <typename T>
+struct MfArgs {
+    const MfFrontDev* fronts;
+    const int* level_fronts;
+    int lvl_off;
+    const int* urows;
+    const int* relpos;
+    const int* children;
+    const int* orig_r;
+    const int* orig_c;
+    const int* orig_k;
+    const int* perm;       // new -> old node
+    const double* Mv;      // CSR values of M_x and A_x
+    const double* Av;
+    const C<T>* shifts;    // s_k
+    int k0;                // first system of the launch
+    C<T>* fac;             // factor blocks; system slot = fac_keep ? k : k - k0
+    long long fac_stride;
+    int fac_keep;
+    C<T>* upd;             // update matrices, slot k - k0
+    long long upd_stride;
+    C<T>* uvec;            // update vectors, slot k - k0
+    long long uvec_stride;
+    C<T>* rhs;             // (systems, n): right-hand sides in, solutions out
+    int n;
+    int* status;
+};
+template <typename T> cudaError_t mf_factor_launch(MfArgs<T> a, int lvl_off, int nfronts, int nsys, cudaStream_t st);
+template <typename T>
+cudaError_t mf_solve_launch(MfArgs<T> a, int lvl_off, int nfronts, int nsys, int max_front, bool fwd, cudaStream_t st);
+
+// CSR spatial operators on the device (general meshes)
+struct CsrDev {
+    int n;
+    const int* rowptr;
+    const int* col;
+    const double* M;
+    const double* A;
+};
+
 // tensor-core (tcgen05, 3xTF32) time transforms
 int tc_round_up(int v, int m);
 bool tc_make_map(CUtensorMap* map, const float* base, int rows, int cols);
@@ -240,4 +287,21 @@ struct st_fdm {
     int factors_valid = 0;        // ws_L holds the factors of all n_t systems (keep mode) or of the kept ones
     int factors_prec = -1;
     unsigned long long wait_probe_ns = 0;   // st_set_wait_probe: copied into the substitution launches
+    // general meshes / sparse-direct spatial solver
+    int spatial = 0;              // 0 = banded LDL^T (structured grids), 1 = multifrontal
+    int* csr_rowptr = nullptr;    // device CSR of M_x, A_x (general meshes; the residual and lifting)
+    int* csr_col = nullptr;
+    double* csr_M = nullptr;
+    double* csr_A = nullptr;
+    stfdm::MfPlan mf;             // host plan
+    stfdm::MfFrontDev* mf_fronts = nullptr;
+    int* mf_ints = nullptr;       // perm, urows, relpos, children, orig_r, orig_c, orig_k, level_fronts
+    const int *mf_perm = nullptr, *mf_urows = nullptr, *mf_relpos = nullptr, *mf_children = nullptr;
+    const int *mf_orig_r = nullptr, *mf_orig_c = nullptr, *mf_orig_k = nullptr, *mf_level = nullptr;
+    double* mf_csrv = nullptr;    // M_x, A_x values on the plan's CSR (structured grids)
+    long long mf_csrv_nnz = 0;
+    void* mf_upd = nullptr;       // update matrices for a chunk of systems
+    size_t mf_upd_bytes = 0;
+    void* mf_uvec = nullptr;      // update vectors for a chunk of systems
+    size_t mf_uvec_bytes = 0;
 };

@@ -183,6 +183,7 @@ extern "C" st_status st_assemble_space(int n_squares, double Lx, double Ly, st_s
 extern "C" st_status st_space_get(const st_space* s, int* m, int* n_x, double* coeffs) {
     if (!s) return fail(ST_ERR_ARG, "st_space_get: NULL handle");
     const SpaceMats& sm = s->sm;
+    if (sm.kind != 0) return fail(ST_ERR_ARG, "st_space_get: not a structured grid (use st_space_get_mesh)");
     if (m) *m = sm.m;
     if (n_x) *n_x = sm.n_x;
     if (coeffs) {

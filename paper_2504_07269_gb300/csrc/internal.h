@@ -29,15 +29,64 @@ struct TimeMats {
     std::vector<double> times;  // DOF times t_1..
 };
 
+// Spatial matrices on a general simplicial mesh: CSR over the interior DOFs (sorted columns, the
+// union pattern of M_x and A_x) and the interior DOFs' coordinates.
+struct MeshSpace {
+    int dim = 0, p = 0, n_x = 0;
+    std::vector<int> rowptr, col;
+    std::vector<double> Mv, Av;
+    std::vector<double> xyz;   // n_x * dim
+};
+
 struct SpaceMats {
+    int kind = 0;      // 0 = structured grid of squares (stencils below), 1 = general mesh (CSR)
     int n = 0;         // squares per direction
     int m = 0;         // interior nodes per direction
-    int n_x = 0;       // m^2
+    int n_x = 0;       // m^2 (structured) or the mesh's interior DOFs
     double Lx = 1, Ly = 1;
     // 7-point stencil coefficients
     double Mc = 0, Mw = 0, Ms = 0, Md = 0;  // centre, W/E, S/N, SW/NE
     double Ac = 0, Aw = 0, As = 0, Ad = 0;
+    MeshSpace mesh;    // kind 1
+    // kind 1, in a solver handle: the device copy of the CSR (set up by st_fdm_setup)
+    const int* d_rowptr = nullptr;
+    const int* d_col = nullptr;
+    const double* d_M = nullptr;
+    const double* d_A = nullptr;
 };
+
+st_status assemble_mesh(int dim, int p, int nv, const double* coords, int nc, const int* cells, MeshSpace& out);
+void structured_as_mesh(const SpaceMats& sm, MeshSpace& out);
+
+// Multifrontal plan of the spatial matrices' sparsity (nested dissection by coordinate bisection,
+// assembly tree of fronts); the same for every shift s_k.  Front p eliminates the `np` pivots
+// first .. first + np - 1 (new numbering) and passes an update matrix on its `nu` update rows
+// (urows, new numbering, ascending) to its parent.  Per system: the factor block of front p is
+// (np + nu) x np column-major at foff; its update matrix nu x nu column-major at uoff (one chunk
+// slot); its update vector at uvoff.
+struct MfFront {
+    int first = 0, np = 0, nu = 0;
+    int parent = -1, height = 0;
+    long long foff = 0, uoff = 0, uvoff = 0;
+    int urows_off = 0;     // urows[urows_off .. + nu)
+    int relpos_off = 0;    // relpos[relpos_off .. + nu): positions of the update rows in the parent's front
+    int orig_off = 0, orig_cnt = 0;   // original entries (local row, local column, CSR index)
+    int child_off = 0, child_cnt = 0; // children[child_off .. + child_cnt)
+};
+
+struct MfPlan {
+    int n = 0;
+    std::vector<int> perm, iperm;      // new -> old, old -> new
+    std::vector<MfFront> fronts;
+    std::vector<int> urows, relpos, children;
+    std::vector<int> orig_r, orig_c, orig_k;
+    std::vector<int> level_ptr, level_fronts;   // fronts by height (leaves first)
+    long long factor_entries = 0, update_entries = 0, uvec_entries = 0;
+    int max_front = 0, max_np = 0;
+    double flops_cmac = 0;             // complex multiply-adds of one factorisation
+};
+
+st_status build_mf_plan(const MeshSpace& ms, int leaf, MfPlan& out);
 
 // host FP64 dense linear algebra (column-major n x n unless stated)
 namespace la {

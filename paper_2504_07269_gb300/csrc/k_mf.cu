@@ -1,0 +1,336 @@
+// Step 3 of the Kronecker solver (Section 3, eq. LGS_x, fast-diagonalisation choice) on general
+// meshes: the n_t independent spatial systems C_k w_k = g_k, C_k = M_x + s_k A_x (complex
+// symmetric), by a sparse direct multifrontal LDL^T factorisation without pivoting (Im s_k < 0
+// makes Im C_k definite, so every principal submatrix is nonsingular in any ordering).  The
+// ordering and assembly tree come from the host plan (nested dissection, host_mf.cpp); every C_k
+// has the same sparsity, so the device work is batched over k.
+//
+// One CTA per (front, system k) and launch level (fronts of equal height in the assembly tree):
+//   factor  the front (np pivots, nu update rows, f = np + nu) is assembled from the entries of
+//           M_x + s_k A_x in its pivot columns and the children's update matrices (extend-add),
+//           then its pivot block is factorised by 32-column panels: the panel's top block by an
+//           unscaled right-looking elimination in shared memory, the rows below by a per-row
+//           substitution against it, the trailing lower triangle by a rank-32 update in 64 x 64
+//           tiles staged in shared memory.  The front lives in global memory: the pivot columns
+//           (f x np, column-major) are the stored factor (L below the diagonal, D on it); the
+//           trailing nu x nu block is the update matrix for the parent.
+//   forward front vector = right-hand side at the pivots + the children's update vectors; the
+//           unit lower pivot block is solved by 32-row blocks (warp 0 by shuffles, the rows below
+//           by all threads); y = z / d goes to the solution, the rest to the update vector.
+//   backward from the root down: the update rows' solutions (ancestors' pivots) are gathered,
+//           the pivot block's transposed system is solved by 32-row blocks from the bottom.
+// Solutions stay in the caller's node order: the kernels index through the permutation.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+
+#include "device.cuh"
+
+namespace stfdm {
+
+template <typename T> struct MfNB;
+template <> struct MfNB<float> { static constexpr int v = 32; };
+template <> struct MfNB<double> { static constexpr int v = 16; };
+
+constexpr int MF_THREADS = 256;
+constexpr int MF_TILE = 64;
+
+template <typename T>
+__device__ __forceinline__ C<T> shfl_c(C<T> v, int src) {
+    return mk<T>(__shfl_sync(0xffffffffu, v.x, src), __shfl_sync(0xffffffffu, v.y, src));
+}
+
+template <typename T>
+__device__ __forceinline__ bool mf_bad(C<T> d) {
+    const T a = fabs(d.x) + fabs(d.y);
+    return !(a > (T)0) || !isfinite(a);
+}
+
+// ------------------------------------------------------------------ factorisation
+template <typename T>
+__global__ void __launch_bounds__(MF_THREADS) k_mf_factor(MfArgs<T> a) {
+    constexpr int NB = MfNB<T>::v;
+    extern __shared__ __align__(16) unsigned char mf_smem[];
+    C<T>* Tt = reinterpret_cast<C<T>*>(mf_smem);            // [NB][NB + 1] top block, row-major
+    C<T>* dinv = Tt + NB * (NB + 1);                         // [NB]
+    C<T>* As = dinv + NB;                                    // [MF_TILE][NB + 1]  rows of the tile
+    C<T>* Bs = As + MF_TILE * (NB + 1);                      // [MF_TILE][NB + 1]  columns (times d)
+    const MfFrontDev fr = a.fronts[a.level_fronts[a.lvl_off + blockIdx.x]];
+    const int k = a.k0 + blockIdx.y;
+    const int tid = threadIdx.x, nth = blockDim.x;
+    const int np = fr.np, nu = fr.nu, f = np + nu;
+    const C<T> s = a.shifts[k];
+    C<T>* Fp = a.fac + (size_t)(a.fac_keep ? k : blockIdx.y) * a.fac_stride + fr.foff;
+    C<T>* S = a.upd + (size_t)blockIdx.y * a.upd_stride + fr.uoff;
+    // entry (r, c), r >= c, of the front
+    auto at = [&](int r, int c) -> C<T>& { return c < np ? Fp[(size_t)c * f + r] : S[(size_t)(c - np) * nu + (r - np)]; };
+
+    // A. assembly
+    for (size_t i = tid; i < (size_t)f * np; i += nth) Fp[i] = mk<T>(0, 0);
+    for (size_t i = tid; i < (size_t)nu * nu; i += nth) S[i] = mk<T>(0, 0);
+    __syncthreads();
+    for (int e = tid; e < fr.orig_cnt; e += nth) {
+        const int q = a.orig_k[fr.orig_off + e];
+        const double m = a.Mv[q], av = a.Av[q];
+        Fp[(size_t)a.orig_c[fr.orig_off + e] * f + a.orig_r[fr.orig_off + e]] =
+            mk<T>((T)(m + (double)s.x * av), (T)((double)s.y * av));
+    }
+    __syncthreads();
+    for (int ci = 0; ci < fr.child_cnt; ++ci) {
+        const MfFrontDev ch = a.fronts[a.children[fr.child_off + ci]];
+        const C<T>* Sc = a.upd + (size_t)blockIdx.y * a.upd_stride + ch.uoff;
+        const int* rp = a.relpos + ch.relpos_off;
+        const int cn = ch.nu;
+        for (int i = tid; i < cn * cn; i += nth) {
+            const int t2 = i / cn, t1 = i - t2 * cn;
+            if (t1 < t2) continue;
+            C<T>& dst = at(rp[t1], rp[t2]);
+            const C<T> v = Sc[i];
+            dst.x += v.x;
+            dst.y += v.y;
+        }
+        __syncthreads();
+    }
+
+    // B. partial LDL^T of the pivot block, panels of NB columns
+    for (int c0 = 0; c0 < np; c0 += NB) {
+        const int w = min(NB, np - c0);
+        for (int i = tid; i < NB * NB; i += nth) {
+            const int r = i / NB, q = i - r * NB;
+            Tt[r * (NB + 1) + q] = (r < w && q <= r) ? Fp[(size_t)(c0 + q) * f + c0 + r] : mk<T>(0, 0);
+        }
+        __syncthreads();
+        // unscaled right-looking elimination of the top block: column q below the diagonal ends as
+        // d_q L(r, q), the diagonal as d_q
+        for (int q = 0; q < w; ++q) {
+            C<T> d = Tt[q * (NB + 1) + q];
+            if (mf_bad<T>(d)) d = mk<T>((T)1e-30, 0);
+            const C<T> di = cinv<T>(d);
+            const int rem = w - q - 1;
+            for (int i = tid; i < rem * rem; i += nth) {
+                const int r = q + 1 + i / rem, c = q + 1 + i % rem;
+                if (c > r) continue;
+                const C<T> lrq = cmul<T>(Tt[r * (NB + 1) + q], di);
+                cfms<T>(Tt[r * (NB + 1) + c], lrq, Tt[c * (NB + 1) + q]);
+            }
+            __syncthreads();
+        }
+        if (tid < w) {
+            C<T> d = Tt[tid * (NB + 1) + tid];
+            if (mf_bad<T>(d)) {
+                atomicExch(a.status, 1);
+                d = mk<T>((T)1e-30, 0);
+                Tt[tid * (NB + 1) + tid] = d;
+            }
+            dinv[tid] = cinv<T>(d);
+        }
+        __syncthreads();
+        for (int i = tid; i < w * w; i += nth) {
+            const int q = i / w, r = i - q * w;
+            if (r < q) continue;
+            Fp[(size_t)(c0 + q) * f + c0 + r] = (r == q) ? Tt[r * (NB + 1) + q] : cmul<T>(Tt[r * (NB + 1) + q], dinv[q]);
+        }
+        // rows below the top block: L(r, q) = (A(r, q) - sum_{q' < q} L(r, q') d_q' L(q, q')) / d_q
+        for (int r = c0 + w + tid; r < f; r += nth) {
+            C<T> l[NB];
+#pragma unroll
+            for (int q = 0; q < NB; ++q) {
+                if (q < w) {
+                    C<T> acc = Fp[(size_t)(c0 + q) * f + r];
+#pragma unroll
+                    for (int q1 = 0; q1 < q; ++q1) cfms<T>(acc, l[q1], Tt[q * (NB + 1) + q1]);
+                    l[q] = cmul<T>(acc, dinv[q]);
+                } else {
+                    l[q] = mk<T>(0, 0);
+                }
+            }
+#pragma unroll
+            for (int q = 0; q < NB; ++q)
+                if (q < w) Fp[(size_t)(c0 + q) * f + r] = l[q];
+        }
+        __syncthreads();
+        // trailing update of the lower triangle of rows / columns [c0 + w, f), 64 x 64 tiles
+        const int base = c0 + w, rem = f - base;
+        const int nt = (rem + MF_TILE - 1) / MF_TILE;
+        const int tx = tid & 15, ty = tid >> 4;
+        for (int tp = 0; tp < nt * (nt + 1) / 2; ++tp) {
+            int I = 0;
+            while ((I + 1) * (I + 2) / 2 <= tp) ++I;
+            const int J = tp - I * (I + 1) / 2;
+            const int rb = base + I * MF_TILE, cb = base + J * MF_TILE;
+            for (int i = tid; i < MF_TILE * NB; i += nth) {
+                const int q = i / MF_TILE, rr = i - q * MF_TILE;
+                const int r = rb + rr, c = cb + rr;
+                As[rr * (NB + 1) + q] = (q < w && r < f) ? Fp[(size_t)(c0 + q) * f + r] : mk<T>(0, 0);
+                Bs[rr * (NB + 1) + q] = (q < w && c < f)
+                                            ? cmul<T>(Fp[(size_t)(c0 + q) * f + c], Tt[q * (NB + 1) + q])
+                                            : mk<T>(0, 0);
+            }
+            __syncthreads();
+            C<T> acc[4][4];
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+#pragma unroll
+                for (int j = 0; j < 4; ++j) acc[i][j] = mk<T>(0, 0);
+            for (int q = 0; q < w; ++q) {
+                C<T> av[4], bv[4];
+#pragma unroll
+                for (int i = 0; i < 4; ++i) av[i] = As[(tx * 4 + i) * (NB + 1) + q];
+#pragma unroll
+                for (int j = 0; j < 4; ++j) bv[j] = Bs[(ty * 4 + j) * (NB + 1) + q];
+#pragma unroll
+                for (int i = 0; i < 4; ++i)
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) cfma<T>(acc[i][j], av[i], bv[j]);
+            }
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                const int c = cb + ty * 4 + j;
+#pragma unroll
+                for (int i = 0; i < 4; ++i) {
+                    const int r = rb + tx * 4 + i;
+                    if (r < f && c < f && r >= c) {
+                        C<T>& dst = at(r, c);
+                        dst = csub<T>(dst, acc[i][j]);
+                    }
+                }
+            }
+            __syncthreads();
+        }
+    }
+}
+
+// ------------------------------------------------------------------ substitutions
+// forward: y = D^{-1} L^{-1} (g + children's update vectors) at the pivots, update vector out
+template <typename T>
+__global__ void __launch_bounds__(MF_THREADS) k_mf_fwd(MfArgs<T> a) {
+    extern __shared__ __align__(16) unsigned char mf_smem[];
+    C<T>* x = reinterpret_cast<C<T>*>(mf_smem);   // [f]
+    const MfFrontDev fr = a.fronts[a.level_fronts[a.lvl_off + blockIdx.x]];
+    const int k = a.k0 + blockIdx.y;
+    const int tid = threadIdx.x, nth = blockDim.x, lane = tid & 31, warp = tid >> 5;
+    const int np = fr.np, nu = fr.nu, f = np + nu;
+    const C<T>* Fp = a.fac + (size_t)(a.fac_keep ? k : blockIdx.y) * a.fac_stride + fr.foff;
+    C<T>* g = a.rhs + (size_t)k * a.n;
+    C<T>* uv = a.uvec + (size_t)blockIdx.y * a.uvec_stride;
+    for (int t = tid; t < f; t += nth) x[t] = t < np ? g[a.perm[fr.first + t]] : mk<T>(0, 0);
+    __syncthreads();
+    for (int ci = 0; ci < fr.child_cnt; ++ci) {
+        const MfFrontDev ch = a.fronts[a.children[fr.child_off + ci]];
+        const int* rp = a.relpos + ch.relpos_off;
+        for (int t = tid; t < ch.nu; t += nth) {
+            const C<T> v = uv[ch.uvoff + t];
+            C<T>& d = x[rp[t]];
+            d.x += v.x;
+            d.y += v.y;
+        }
+        __syncthreads();
+    }
+    for (int q0 = 0; q0 < np; q0 += 32) {
+        const int wq = min(32, np - q0);
+        if (warp == 0) {
+            C<T> v = lane < wq ? x[q0 + lane] : mk<T>(0, 0);
+            for (int q = 0; q < wq; ++q) {
+                const C<T> z = shfl_c<T>(v, q);
+                if (lane > q && lane < wq) cfms<T>(v, Fp[(size_t)(q0 + q) * f + q0 + lane], z);
+            }
+            if (lane < wq) x[q0 + lane] = v;
+        }
+        __syncthreads();
+        for (int r = q0 + wq + tid; r < f; r += nth) {
+            C<T> acc = x[r];
+            for (int q = 0; q < wq; ++q) cfms<T>(acc, Fp[(size_t)(q0 + q) * f + r], x[q0 + q]);
+            x[r] = acc;
+        }
+        __syncthreads();
+    }
+    for (int t = tid; t < np; t += nth) g[a.perm[fr.first + t]] = cmul<T>(x[t], cinv<T>(Fp[(size_t)t * f + t]));
+    for (int t = tid; t < nu; t += nth) uv[fr.uvoff + t] = x[np + t];
+}
+
+// backward: L^T w = y over the pivot block, with the update rows' solutions known
+template <typename T>
+__global__ void __launch_bounds__(MF_THREADS) k_mf_bwd(MfArgs<T> a) {
+    extern __shared__ __align__(16) unsigned char mf_smem[];
+    C<T>* x = reinterpret_cast<C<T>*>(mf_smem);   // [f]
+    const MfFrontDev fr = a.fronts[a.level_fronts[a.lvl_off + blockIdx.x]];
+    const int k = a.k0 + blockIdx.y;
+    const int tid = threadIdx.x, nth = blockDim.x, lane = tid & 31, warp = tid >> 5, nwarps = nth >> 5;
+    const int np = fr.np, nu = fr.nu, f = np + nu;
+    const C<T>* Fp = a.fac + (size_t)(a.fac_keep ? k : blockIdx.y) * a.fac_stride + fr.foff;
+    C<T>* g = a.rhs + (size_t)k * a.n;
+    for (int t = tid; t < f; t += nth)
+        x[t] = g[a.perm[t < np ? fr.first + t : a.urows[fr.urows_off + t - np]]];
+    __syncthreads();
+    for (int q0 = ((np - 1) / 32) * 32; q0 >= 0; q0 -= 32) {
+        const int wq = min(32, np - q0);
+        // contributions of the solved rows below the block: one warp per column
+        for (int q = warp; q < wq; q += nwarps) {
+            const C<T>* col = Fp + (size_t)(q0 + q) * f;
+            C<T> acc = mk<T>(0, 0);
+            for (int r = q0 + wq + lane; r < f; r += 32) cfma<T>(acc, col[r], x[r]);
+#pragma unroll
+            for (int off = 16; off > 0; off >>= 1) {
+                acc.x += __shfl_xor_sync(0xffffffffu, acc.x, off);
+                acc.y += __shfl_xor_sync(0xffffffffu, acc.y, off);
+            }
+            if (lane == 0) x[q0 + q] = csub<T>(x[q0 + q], acc);
+        }
+        __syncthreads();
+        if (warp == 0) {
+            C<T> v = lane < wq ? x[q0 + lane] : mk<T>(0, 0);
+            for (int i = wq - 1; i >= 0; --i) {
+                const C<T> wi = shfl_c<T>(v, i);
+                if (lane < i) cfms<T>(v, Fp[(size_t)(q0 + lane) * f + q0 + i], wi);
+            }
+            if (lane < wq) x[q0 + lane] = v;
+        }
+        __syncthreads();
+    }
+    for (int t = tid; t < np; t += nth) g[a.perm[fr.first + t]] = x[t];
+}
+
+// ------------------------------------------------------------------ launchers
+template <typename T>
+size_t mf_factor_smem() {
+    constexpr int NB = MfNB<T>::v;
+    return sizeof(C<T>) * ((size_t)NB * (NB + 1) + NB + 2 * (size_t)MF_TILE * (NB + 1));
+}
+
+template <typename T>
+cudaError_t mf_factor_launch(MfArgs<T> a, int lvl_off, int nfronts, int nsys, cudaStream_t st) {
+    if (nfronts <= 0 || nsys <= 0) return cudaSuccess;
+    a.lvl_off = lvl_off;
+    const size_t smem = mf_factor_smem<T>();
+    cudaError_t e = cudaFuncSetAttribute(k_mf_factor<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    k_mf_factor<T><<<dim3(nfronts, nsys), MF_THREADS, smem, st>>>(a);
+    note_launches(1);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t mf_solve_launch(MfArgs<T> a, int lvl_off, int nfronts, int nsys, int max_front, bool fwd, cudaStream_t st) {
+    if (nfronts <= 0 || nsys <= 0) return cudaSuccess;
+    a.lvl_off = lvl_off;
+    const size_t smem = sizeof(C<T>) * (size_t)max_front;
+    cudaError_t e;
+    if (fwd) {
+        e = cudaFuncSetAttribute(k_mf_fwd<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        k_mf_fwd<T><<<dim3(nfronts, nsys), MF_THREADS, smem, st>>>(a);
+    } else {
+        e = cudaFuncSetAttribute(k_mf_bwd<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        k_mf_bwd<T><<<dim3(nfronts, nsys), MF_THREADS, smem, st>>>(a);
+    }
+    note_launches(1);
+    return cudaGetLastError();
+}
+
+template cudaError_t mf_factor_launch<float>(MfArgs<float>, int, int, int, cudaStream_t);
+template cudaError_t mf_factor_launch<double>(MfArgs<double>, int, int, int, cudaStream_t);
+template cudaError_t mf_solve_launch<float>(MfArgs<float>, int, int, int, int, bool, cudaStream_t);
+template cudaError_t mf_solve_launch<double>(MfArgs<double>, int, int, int, int, bool, cudaStream_t);
+
+}  // namespace stfdm

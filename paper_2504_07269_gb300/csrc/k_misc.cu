@@ -39,9 +39,33 @@ __device__ __forceinline__ void stencil_MA(const Stencil& s, const C<TI>* u, int
     Qa.y = s.Ac * c.y + s.Aw * we.y + s.As * sn.y + s.Ad * dg.y;
 }
 
-// out[x] = (add ? add[x] : 0) + sign * (A_x in)[x]
+// General meshes: M_x and A_x in CSR over the interior DOFs (one pattern for both).
+struct Csr {
+    int m;   // unused (keeps the interface of Stencil)
+    const int* rowptr;
+    const int* col;
+    const double* M;
+    const double* A;
+};
+
 template <typename TI>
-__global__ void k_stencil_A(Stencil s, int n_x, const C<TI>* in, const double2* add, double sign, double2* out) {
+__device__ __forceinline__ void stencil_MA(const Csr& s, const C<TI>* u, int x, double2& Pm, double2& Qa) {
+    double2 p = make_double2(0, 0), q = make_double2(0, 0);
+    for (int e = s.rowptr[x]; e < s.rowptr[x + 1]; ++e) {
+        const C<TI> v = u[s.col[e]];
+        const double mv = s.M[e], av = s.A[e];
+        p.x += mv * (double)v.x;
+        p.y += mv * (double)v.y;
+        q.x += av * (double)v.x;
+        q.y += av * (double)v.y;
+    }
+    Pm = p;
+    Qa = q;
+}
+
+// out[x] = (add ? add[x] : 0) + sign * (A_x in)[x]
+template <typename TI, typename Op>
+__global__ void k_stencil_A(Op s, int n_x, const C<TI>* in, const double2* add, double sign, double2* out) {
     int x = blockIdx.x * blockDim.x + threadIdx.x;
     if (x >= n_x) return;
     double2 P, Q;
@@ -52,9 +76,10 @@ __global__ void k_stencil_A(Stencil s, int n_x, const C<TI>* in, const double2* 
     out[x] = r;
 }
 
+template <typename Op>
 struct ResArgs {
     int n_t, n_x;
-    Stencil s;
+    Op s;
     const double* Mb;   // n_t x 5 band of M_t
     const double* Bb;   // n_t x 5 band of B_t (or B_t^T)
     double bsign;       // +1: K;  -1 with B_t^T: K^H
@@ -82,8 +107,8 @@ __device__ __forceinline__ double block_sum(double v, double* red) {
 }
 
 // TB: nonzero diagonals of the temporal bands (3 for P1 time, 5 for P2)
-template <int TB>
-__global__ void __launch_bounds__(256) k_residual(ResArgs a) {
+template <int TB, typename Op>
+__global__ void __launch_bounds__(256) k_residual(ResArgs<Op> a) {
     __shared__ double red[32];
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
     const int l0 = blockIdx.y * RES_LT;
@@ -183,7 +208,8 @@ __global__ void k_add_row(int n_t, int n_x, C<T>* psi, const C<T>* psi0) {
 }
 
 // F[l, x] = sum_k Mfull[l+1, k] (M_x f_k)[x] over full time indices k (t_0 included)
-__global__ void k_load_nodal(int n_t, int n_x, Stencil s, const double* Mb, const double* Mfull0,
+template <typename Op>
+__global__ void k_load_nodal(int n_t, int n_x, Op s, const double* Mb, const double* Mfull0,
                              const double2* f, double2* F) {
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
     const int l = blockIdx.y;
@@ -231,28 +257,37 @@ __global__ void k_colsums(int n_t, int n_x, const double2* U1, const double2* U2
 static Stencil make_stencil(const SpaceMats& sm) {
     return Stencil{sm.m, sm.Mc, sm.Mw, sm.Ms, sm.Md, sm.Ac, sm.Aw, sm.As, sm.Ad};
 }
+static Csr make_csr(const SpaceMats& sm) { return Csr{0, sm.d_rowptr, sm.d_col, sm.d_M, sm.d_A}; }
+
+template <typename Op>
+static cudaError_t stencil_A_op(const Op& s, int n_x, const void* in, bool in_c64, const double2* add, double sign,
+                                double2* out, cudaStream_t st) {
+    int grid = (n_x + 255) / 256;
+    if (in_c64) k_stencil_A<float, Op><<<grid, 256, 0, st>>>(s, n_x, (const float2*)in, add, sign, out);
+    else k_stencil_A<double, Op><<<grid, 256, 0, st>>>(s, n_x, (const double2*)in, add, sign, out);
+    note_launches(1);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_stencil_A(const SpaceMats& sm, const void* in, bool in_c64, const double2* add, double sign,
                              double2* out, cudaStream_t st) {
-    Stencil s = make_stencil(sm);
-    int grid = (sm.n_x + 255) / 256;
-    if (in_c64) k_stencil_A<float><<<grid, 256, 0, st>>>(s, sm.n_x, (const float2*)in, add, sign, out);
-    else k_stencil_A<double><<<grid, 256, 0, st>>>(s, sm.n_x, (const double2*)in, add, sign, out);
-    note_launches(1);
-    return cudaGetLastError();
+    if (sm.kind == 1) return stencil_A_op(make_csr(sm), sm.n_x, in, in_c64, add, sign, out, st);
+    return stencil_A_op(make_stencil(sm), sm.n_x, in, in_c64, add, sign, out, st);
 }
 
 int residual_num_partials(int n_t, int n_x) {
     return ((n_x + 255) / 256) * ((n_t + RES_LT - 1) / RES_LT);
 }
 
-cudaError_t launch_residual(const SpaceMats& sm, int n_t, int time_band, const double* Mb, const double* Bb, double bsign,
-                            const double2* F, const double2* apsi0, const double* m_t, const double2* U,
-                            const double2* psi0, double2* R, double* partials, double* scalars, cudaStream_t st) {
-    ResArgs a;
+template <typename Op>
+static cudaError_t residual_op(const Op& op, const SpaceMats& sm, int n_t, int time_band, const double* Mb,
+                               const double* Bb, double bsign, const double2* F, const double2* apsi0, const double* m_t,
+                               const double2* U, const double2* psi0, double2* R, double* partials, double* scalars,
+                               cudaStream_t st) {
+    ResArgs<Op> a;
     a.n_t = n_t;
     a.n_x = sm.n_x;
-    a.s = make_stencil(sm);
+    a.s = op;
     a.Mb = Mb;
     a.Bb = Bb;
     a.bsign = bsign;
@@ -264,13 +299,22 @@ cudaError_t launch_residual(const SpaceMats& sm, int n_t, int time_band, const d
     a.R = R;
     a.partials = partials;
     dim3 grid((sm.n_x + 255) / 256, (n_t + RES_LT - 1) / RES_LT);
-    if (time_band == 3) k_residual<3><<<grid, 256, 0, st>>>(a);
-    else k_residual<5><<<grid, 256, 0, st>>>(a);
+    if (time_band == 3) k_residual<3, Op><<<grid, 256, 0, st>>>(a);
+    else k_residual<5, Op><<<grid, 256, 0, st>>>(a);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     k_reduce_finalize<<<1, 256, 0, st>>>(partials, (int)(grid.x * grid.y), scalars, (double)n_t * sm.n_x);
     note_launches(2);
     return cudaGetLastError();
+}
+
+cudaError_t launch_residual(const SpaceMats& sm, int n_t, int time_band, const double* Mb, const double* Bb, double bsign,
+                            const double2* F, const double2* apsi0, const double* m_t, const double2* U,
+                            const double2* psi0, double2* R, double* partials, double* scalars, cudaStream_t st) {
+    if (sm.kind == 1)
+        return residual_op(make_csr(sm), sm, n_t, time_band, Mb, Bb, bsign, F, apsi0, m_t, U, psi0, R, partials, scalars, st);
+    return residual_op(make_stencil(sm), sm, n_t, time_band, Mb, Bb, bsign, F, apsi0, m_t, U, psi0, R, partials, scalars,
+                       st);
 }
 
 cudaError_t launch_add_row(int n_t, int n_x, void* psi, const void* psi0, bool c64, cudaStream_t st) {
@@ -285,7 +329,8 @@ cudaError_t launch_add_row(int n_t, int n_x, void* psi, const void* psi0, bool c
 cudaError_t launch_load_nodal(const SpaceMats& sm, int n_t, const double* Mb, const double* Mfull0,
                               const double2* f, double2* F, cudaStream_t st) {
     dim3 grid((sm.n_x + 255) / 256, n_t);
-    k_load_nodal<<<grid, 256, 0, st>>>(n_t, sm.n_x, make_stencil(sm), Mb, Mfull0, f, F);
+    if (sm.kind == 1) k_load_nodal<Csr><<<grid, 256, 0, st>>>(n_t, sm.n_x, make_csr(sm), Mb, Mfull0, f, F);
+    else k_load_nodal<Stencil><<<grid, 256, 0, st>>>(n_t, sm.n_x, make_stencil(sm), Mb, Mfull0, f, F);
     note_launches(1);
     return cudaGetLastError();
 }

@@ -166,6 +166,7 @@ using namespace stfdm;
 extern "C" st_status st_residual_noalloc(const st_fdm* h, const void* F, const void* psi0, const void* psi, void* R,
                                          double* norms, void* stream) {
     if (!h || !F || !psi || !norms) return fail(ST_ERR_ARG, "st_residual_noalloc: NULL argument");
+    if (h->sm.kind != 0) return fail(ST_ERR_UNSUPPORTED, "st_residual_noalloc: structured grids only");
     // R is written while other threads still read the stencil neighbours of psi and psi0
     if (R && (R == psi || R == psi0)) return fail(ST_ERR_ARG, "st_residual_noalloc: R must not alias psi or psi0");
     const int n_t = h->tm.n_t, n_x = h->sm.n_x;

@@ -360,6 +360,7 @@ using namespace stfdm;
 extern "C" st_status st_error_norms(st_fdm* h, int exact, const void* psi, const void* psi0, int q_t, int q_x,
                                     double* out, void* stream) {
     if (!h || !psi || !out) return fail(ST_ERR_ARG, "st_error_norms: NULL argument");
+    if (h->sm.kind != 0) return fail(ST_ERR_UNSUPPORTED, "st_error_norms: structured grids only");
     if (exact != ST_EXACT_C1 && exact != ST_EXACT_PAPER) return fail(ST_ERR_ARG, "st_error_norms: unknown solution");
     if (h->tm.p != 1 && h->tm.p != 2) return fail(ST_ERR_UNSUPPORTED, "st_error_norms: temporal degree 1 or 2");
     if (h->tm.N > 65535) return fail(ST_ERR_UNSUPPORTED, "st_error_norms: more than 65535 time elements");
@@ -418,6 +419,7 @@ extern "C" st_status st_error_norms(st_fdm* h, int exact, const void* psi, const
 
 extern "C" st_status st_load_quadrature(st_fdm* h, int exact, int q_t, int q_x, void* F, void* stream) {
     if (!h || !F) return fail(ST_ERR_ARG, "st_load_quadrature: NULL argument");
+    if (h->sm.kind != 0) return fail(ST_ERR_UNSUPPORTED, "st_load_quadrature: structured grids only");
     if (exact != ST_EXACT_C1 && exact != ST_EXACT_PAPER) return fail(ST_ERR_ARG, "st_load_quadrature: unknown solution");
     if (h->tm.p != 1 && h->tm.p != 2) return fail(ST_ERR_UNSUPPORTED, "st_load_quadrature: temporal degree 1 or 2");
     if (h->tm.n_t > 65535) return fail(ST_ERR_UNSUPPORTED, "st_load_quadrature: n_t > 65535");

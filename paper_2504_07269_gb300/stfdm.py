@@ -180,9 +180,62 @@ def st_time_decompose(t: TimeHandle, host_threads: int = 0):
     return X, s, Y, k.value
 
 
+SPATIAL = {"auto": _lib.ST_SPATIAL_AUTO, "banded": _lib.ST_SPATIAL_BANDED,
+           "multifrontal": _lib.ST_SPATIAL_MULTIFRONTAL}
+
+
+def st_assemble_mesh(dim: int, p_x: int, coords, cells) -> SpaceHandle:
+    """Spatial P1/P2 matrices on a triangle (dim 2) or tetrahedron (dim 3) mesh; coords (V, dim)
+    floats, cells (C, dim + 1) vertex indices."""
+    c = np.ascontiguousarray(np.asarray(coords, dtype=np.float64))
+    e = np.ascontiguousarray(np.asarray(cells, dtype=np.int32))
+    if c.ndim != 2 or c.shape[1] != dim or e.ndim != 2 or e.shape[1] != dim + 1:
+        raise ValueError("coords must be (V, dim) and cells (C, dim + 1)")
+    out = ctypes.c_void_p()
+    check(lib().st_assemble_mesh(int(dim), int(p_x), c.shape[0], c.ctypes.data_as(ctypes.c_void_p), e.shape[0],
+                                 e.ctypes.data_as(ctypes.c_void_p), ctypes.byref(out)), "st_assemble_mesh")
+    return SpaceHandle(out)
+
+
+def st_space_get_mesh(s: SpaceHandle):
+    """CSR (rowptr, col, M, A) of the interior DOFs and their coordinates xyz (n_x, dim)."""
+    dim, p, n, nnz = ctypes.c_int(), ctypes.c_int(), ctypes.c_int(), ctypes.c_longlong()
+    check(lib().st_space_get_mesh(s.ptr, ctypes.byref(dim), ctypes.byref(p), ctypes.byref(n), ctypes.byref(nnz),
+                                  None, None, None, None, None), "st_space_get_mesh")
+    rp = np.zeros(n.value + 1, dtype=np.int32)
+    col = np.zeros(nnz.value, dtype=np.int32)
+    M = np.zeros(nnz.value)
+    A = np.zeros(nnz.value)
+    xyz = np.zeros((n.value, dim.value))
+    ptr = lambda a: a.ctypes.data_as(ctypes.c_void_p)   # noqa: E731
+    check(lib().st_space_get_mesh(s.ptr, None, None, None, None, ptr(rp), ptr(col), ptr(M), ptr(A), ptr(xyz)),
+          "st_space_get_mesh")
+    return dict(dim=dim.value, p_x=p.value, n_x=n.value, rowptr=rp, col=col, M=M, A=A, xyz=xyz)
+
+
+def st_space_mf_plan(s: SpaceHandle, leaf: int = 0):
+    """Statistics and structure of the sparse-direct solver's plan for a space."""
+    nf, nl, mf = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+    fe, fl = ctypes.c_longlong(), ctypes.c_double()
+    check(lib().st_space_mf_plan(s.ptr, int(leaf), ctypes.byref(nf), ctypes.byref(nl), ctypes.byref(mf),
+                                 ctypes.byref(fe), ctypes.byref(fl), None, None, None, None, None), "st_space_mf_plan")
+    F = nf.value
+    info = st_space_get_mesh(s)
+    perm = np.zeros(info["n_x"], dtype=np.int32)
+    first, npv, nu = (np.zeros(F, dtype=np.int32) for _ in range(3))
+    ptr = lambda a: a.ctypes.data_as(ctypes.c_void_p)   # noqa: E731
+    check(lib().st_space_mf_plan(s.ptr, int(leaf), None, None, None, None, None, ptr(perm), ptr(first), ptr(npv),
+                                 ptr(nu), None), "st_space_mf_plan")
+    urows = np.zeros(int(nu.sum()), dtype=np.int32)
+    check(lib().st_space_mf_plan(s.ptr, int(leaf), None, None, None, None, None, None, None, None, None, ptr(urows)),
+          "st_space_mf_plan")
+    return dict(fronts=F, levels=nl.value, max_front=mf.value, factor_entries=fe.value, flops=fl.value, perm=perm,
+                first=first, np=npv, nu=nu, urows=urows)
+
+
 def st_fdm_setup(t: TimeHandle, s: SpaceHandle, kappa_max: float = 0.0, device: int = -1,
-                 host_threads: int = 0) -> FdmHandle:
-    opts = _lib.st_setup_opts(float(kappa_max), int(device), int(host_threads))
+                 host_threads: int = 0, spatial_solver: str = "auto") -> FdmHandle:
+    opts = _lib.st_setup_opts(float(kappa_max), int(device), int(host_threads), SPATIAL[spatial_solver])
     out = ctypes.c_void_p()
     check(lib().st_fdm_setup(t.ptr, s.ptr, ctypes.byref(opts), ctypes.byref(out)), "st_fdm_setup")
     return FdmHandle(out, t, s, int(device) if device >= 0 else torch.cuda.current_device())
@@ -419,6 +472,13 @@ def setup_problem(n_squares: int, p_t: int, t_nodes, Lx: float = 1.0, Ly: float 
     """assemble_time + assemble_space + fdm_setup in one call."""
     t = st_assemble_time(p_t, t_nodes)
     s = st_assemble_space(n_squares, Lx, Ly)
+    return st_fdm_setup(t, s, **kw)
+
+
+def setup_mesh_problem(dim: int, p_x: int, coords, cells, p_t: int, t_nodes, **kw) -> FdmHandle:
+    """assemble_time + assemble_mesh + fdm_setup in one call (general meshes)."""
+    t = st_assemble_time(p_t, t_nodes)
+    s = st_assemble_mesh(dim, p_x, coords, cells)
     return st_fdm_setup(t, s, **kw)
 
 
