@@ -56,6 +56,8 @@ def parse_args(argv=None):
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--config", default="c3")
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64", "fp32"])
+    ap.add_argument("--spatial", default="banded", choices=["banded", "multifrontal"],
+                    help="spatial solver of step 3: banded LDL^T (default) or the sparse-direct multifrontal one")
     ap.add_argument("--no-fp64-check", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--profile-step", action="store_true",
@@ -277,7 +279,8 @@ def _config(pr, args):
     gb = pr.unknowns * 16 / 1e9
     return {"workload": f"{pr.n}x{pr.n} squares P1 space ({pr.n_x} nodes), P{pr.p_t} time {len(pr.t_nodes) - 1} "
                         f"uniform elements (n_t={pr.n_t}), T={pr.t_nodes[-1]:g}; {pr.unknowns} unknowns; {inputs}",
-            "name": pr.name, "precision": args.precision, "tol": single_tol(pr), "n_x": pr.n_x, "n_t": pr.n_t,
+            "name": pr.name, "precision": args.precision, "spatial_solver": getattr(args, "spatial", "banded"),
+            "tol": single_tol(pr), "n_x": pr.n_x, "n_t": pr.n_t,
             "unknowns": pr.unknowns, "l2_flush": f"inputs ({gb:.2f} GB c128 load) larger than the 129 MB L2",
             "parallelism": "replicas" if args.gpus > 1 else "single GPU"}
 
@@ -298,7 +301,7 @@ def run_ours(args):
     pr = synth.config_problem(args.config)
     tol = single_tol(pr)
     t0 = time.perf_counter()
-    h = stfdm.setup_problem(pr.n, pr.p_t, pr.t_nodes, Lx=pr.Lx, Ly=pr.Ly, device=local)
+    h = stfdm.setup_problem(pr.n, pr.p_t, pr.t_nodes, Lx=pr.Lx, Ly=pr.Ly, device=local, spatial_solver=args.spatial)
     setup_s = time.perf_counter() - t0
     F, p0 = make_inputs(pr, h, dev)
     dt = torch.complex64 if args.precision == "fp32" else torch.complex128
@@ -423,19 +426,30 @@ def run_ours(args):
         times.append(e0.elapsed_time(e1) * 1e-3)
     tk = statistics.median(times)
     b = pr.n - 1 + 1
-    # complex MAC = 8 real flops; per system n_x b^2/2 for the factorisation and n_x b for each of
-    # the two substitutions (the forward one fused into the factor kernel, the backward one a
-    # separate launch inside the timed region)
-    flops = 8.0 * pr.n_t * pr.n_x * (b * b / 2.0 + 2.0 * b)
+    if args.spatial == "multifrontal":
+        # the plan's factorisation flops (8 per complex multiply-add over every front's eliminations)
+        # plus both substitutions over the stored factor blocks, per system
+        plan = stfdm.st_space_mf_plan(h.space, 64)
+        flops = pr.n_t * (plan["flops"] + 2.0 * 8.0 * plan["factor_entries"])
+    else:
+        # complex MAC = 8 real flops; per system n_x b^2/2 for the factorisation and n_x b for each of
+        # the two substitutions (the forward one fused into the factor kernel, the backward one a
+        # separate launch inside the timed region)
+        flops = 8.0 * pr.n_t * pr.n_x * (b * b / 2.0 + 2.0 * b)
     props = torch.cuda.get_device_properties(dev)
     max_mhz = (clocks or {}).get("sm_max_mhz") or (measured_peaks() or {}).get("sm_max_mhz", 2070.0)
     lanes = 128 if kprec == "fp32" else 2             # FP32 / FP64 FMA lanes per SM per clock
     peak = props.multi_processor_count * lanes * 2 * max_mhz * 1e6 / 1e12
     achieved = flops / tk / 1e12
-    roof = {"bound": "alu", "kernel": "k_band_factor_v4 (complex64, fused forward substitution) + k_subst_bwd<float>" if kprec == "fp32"
-            else "k_band_factor_solve<double,32> + k_subst_bwd<double>",
+    if args.spatial == "multifrontal":
+        kname = f"k_mf_factor<{'float' if kprec == 'fp32' else 'double'}> + k_mf_fwd + k_mf_bwd (all levels)"
+    elif kprec == "fp32":
+        kname = "k_band_factor_v4 (complex64, fused forward substitution) + k_subst_bwd<float>"
+    else:
+        kname = "k_band_factor_solve<double,32> + k_subst_bwd<double>"
+    roof = {"bound": "alu", "kernel": kname,
             "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-            "traffic": profiled_traffic(args.config), "launch_ms": tk * 1e3,
+            "traffic": profiled_traffic(args.config) if args.spatial == "banded" else None, "launch_ms": tk * 1e3,
             "peak_basis": f"{props.multi_processor_count} SMs x {lanes} {kprec.upper()} FMA lanes x 2 x {max_mhz:.0f} MHz "
                           "(derived, max SM clock)"}
 

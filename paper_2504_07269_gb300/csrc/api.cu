@@ -533,9 +533,28 @@ st_status ensure_common(st_fdm* h) {
 
 double2* vec_slot(st_fdm* h, int i) { return reinterpret_cast<double2*>(h->ws_vec) + (size_t)i * h->sm.n_x; }
 
+// A direct (single-application) solve needs neither the refinement's basis nor the partial keep's
+// transient wave: release them, so that its own transient factors find the memory.
+void release_refinement_workspace(st_fdm* h) {
+    const bool busy = h->ws_kry || h->ws_Lt || h->ws_Dt;
+    if (!busy) return;
+    cudaFree(h->ws_kry);   // cudaFree waits for the device work in flight, like grow()'s reallocations
+    h->ws_kry = nullptr;
+    h->ws_kry_bytes = 0;
+    h->kry_m = 0;
+    cudaFree(h->ws_Lt);
+    h->ws_Lt = nullptr;
+    h->ws_Lt_bytes = 0;
+    cudaFree(h->ws_Dt);
+    h->ws_Dt = nullptr;
+    h->ws_Dt_bytes = 0;
+    h->kept_sys = 0;
+}
+
 // ------------------------------------------------------------------ solves
 st_status solve_fp64(st_fdm* h, const void* F, const void* psi0, void* psi, cudaStream_t st) {
     const int n_t = h->tm.n_t, n_x = h->sm.n_x;
+    release_refinement_workspace(h);
     st_status s = ensure_common(h);
     if (s != ST_OK) return s;
     s = grow(h->ws_big, h->ws_big_bytes, (size_t)n_t * n_x * sizeof(double2), "G");
@@ -557,6 +576,7 @@ st_status solve_fp64(st_fdm* h, const void* F, const void* psi0, void* psi, cuda
 
 st_status solve_fp32(st_fdm* h, const void* F, const void* psi0, void* psi, cudaStream_t st) {
     const int n_t = h->tm.n_t, n_x = h->sm.n_x;
+    release_refinement_workspace(h);
     st_status s = ensure_common(h);
     if (s != ST_OK) return s;
     s = grow(h->ws_g32, h->ws_g32_bytes, (size_t)n_t * n_x * sizeof(float2), "G32");
@@ -888,6 +908,7 @@ st_status solve_mixed_gmres(st_fdm* h, bool adjoint, const void* F, const void* 
 
 st_status adjoint_direct(st_fdm* h, bool fp32, const void* G, void* lambda, cudaStream_t st) {
     const int n_t = h->tm.n_t, n_x = h->sm.n_x;
+    release_refinement_workspace(h);
     st_status s;
     if (!fp32) {
         s = grow(h->ws_big, h->ws_big_bytes, (size_t)n_t * n_x * sizeof(double2), "H");
@@ -1296,6 +1317,7 @@ extern "C" st_status st_spatial_solve(st_fdm* h, int precision, const void* G, v
     const size_t esz = precision == ST_FP64 ? sizeof(double2) : sizeof(float2);
     if (precision != ST_FP64 && precision != ST_FP32 && precision != ST_MIXED)
         return fail(ST_ERR_ARG, "st_spatial_solve: unknown precision");
+    release_refinement_workspace(h);
     if (W != G) CUDA_TRY(cudaMemcpyAsync(W, G, elems * esz, cudaMemcpyDeviceToDevice, st));
     CUDA_TRY(cudaMemsetAsync(h->ws_status, 0, 2 * sizeof(int), st));
     st_status s = (precision == ST_FP64) ? band_run<double>(h, reinterpret_cast<double2*>(W), 0, st)

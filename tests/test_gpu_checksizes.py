@@ -78,7 +78,10 @@ def test_wide_band_vs_refined_cpu_fdm(dev, n, p, N):
     assert h.m + 1 == n and h.m + 1 > 256
     Fd, p0 = torch.from_numpy(F).to(dev), torch.from_numpy(psi0).to(dev)
     psi64, _ = stfdm.st_fdm_solve(h, Fd, p0, precision="fp64")
-    psim, info = stfdm.st_fdm_solve(h, Fd, p0, precision="mixed")
+    # the discrete manufactured solution is white noise, with as much weight on the operator's small
+    # singular directions as on any other, so the error/residual ratio approaches cond(K) (~1e5 at
+    # these bands): refine to 1e-13
+    psim, info = stfdm.st_fdm_solve(h, Fd, p0, precision="mixed", tol=1e-13, max_sweeps=60)
     e64, em = rel(psi64.cpu().numpy(), ref), rel(psim.cpu().numpy(), ref)
     exact = u + psi0[None, :]
     print(f"b={n} P{p} n_t={p * N} ({u.size} unknowns): oracle residuals {rep['residuals']}, oracle vs u* "

@@ -107,10 +107,12 @@ def test_c4_adjoint_gradient_vs_finite_differences():
     alpha = 1e-3, target and psi0 seeded packets (128x128 squares, P1 time N_t = 256, T = 1).
     The gradient W K^{-H} W e + alpha W f (one adjoint solve) against central differences of J
     (two forward solves each) along 20 seeded complex directions (|d| = |f|).  J is quadratic in f,
-    so the difference quotient has no truncation error for any step; its only error is the forward
-    solves' rounding divided by h.  At h = 1e-3 the plain FP64 FDM (rounding about 1e-11 relative,
-    kappa_2(X_t) eps) checks the gradient to 1e-6; at the configured h = 1e-6 the forward solves
-    are refined to a 1e-13 FP64 residual, and the bar is 1e-6 on all 20 directions."""
+    so the difference quotient has no truncation error for any step; its error is rounding divided
+    by h: that of the forward solves and that of J's own evaluation.  At h = 1e-3 the plain FP64 FDM
+    and plainly summed J values check the gradient to 1e-6.  At the configured h = 1e-6 the forward
+    solves are refined to a 1e-13 FP64 residual and J(f + h d) - J(f - h d) is formed as one sum of
+    differences (the same quantity, without the cancellation of two large sums); the bar is 1e-6 on
+    all 20 directions."""
     if not torch.cuda.is_available():
         pytest.skip("no CUDA device")
     from paper_2504_07269_gb300 import build, stfdm
@@ -151,10 +153,21 @@ def test_c4_adjoint_gradient_vs_finite_differences():
     for i in range(20):
         d = synth.cn01(f.shape, seed=1000 + i)
         dirs.append(d * (np.linalg.norm(f) / np.linalg.norm(d)))
+    def J_diff(fp, fm, precision):
+        # J(fp) - J(fm) with the two quadratic forms subtracted before they are summed:
+        # a^H W a - b^H W b = Re (a - b)^H W (a + b) for Hermitian W.  J itself is dominated by terms
+        # that do not change along d, so subtracting two summed J values loses about |J| eps sqrt(n)
+        # to rounding, which 1/h amplifies far beyond the bar at h = 1e-6.
+        ep, em = forward(fp, precision) - target, forward(fm, precision) - target
+        return 0.5 * wdot(ep - em, ep + em).real + 0.5 * alpha * wdot(fp - fm, fp + fm).real
+
     for hstep, ndir, bar, prec in ((1e-3, 20, 1e-6, "fp64"), (1e-6, 20, 1e-6, "mixed")):
         gaps = []
         for d in dirs[:ndir]:
-            fd = (J(f + hstep * d, prec) - J(f - hstep * d, prec)) / (2 * hstep)
+            if prec == "fp64":
+                fd = (J(f + hstep * d, prec) - J(f - hstep * d, prec)) / (2 * hstep)
+            else:
+                fd = J_diff(f + hstep * d, f - hstep * d, prec) / (2 * hstep)
             ad = np.vdot(g, d).real
             gaps.append(abs(fd - ad) / abs(ad))
         print(f"c4 adjoint gradient vs central differences, h = {hstep:g} ({ndir} directions, forward solves "

@@ -322,7 +322,7 @@ def test_bounded_wait_times_out_and_handle_recovers(dev):
     _, s, _, _ = stfdm.st_time_decompose(h.time)
     for k in range(h.n_t):
         ref = spla.splu(sp.csc_matrix(M_x + s[k] * A_x, dtype=np.complex128)).solve(G[k])
-        assert rel(W[k], ref) <= 1e-4
+        assert rel(W[k], ref) <= 1e-3          # FP32: cond(C_k) u_32
     F = synth.cn01((h.n_t, h.n_x), seed=22)
     ref = solve.solve_explicit(_oracle_K(n, p, t), F)
     psi, _ = stfdm.st_fdm_solve(h, torch.from_numpy(F).to(dev), precision="mixed")
