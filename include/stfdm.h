@@ -209,6 +209,17 @@ st_status st_fdm_get(const st_fdm* h, int* n_t, int* n_x, int* m, double* kappa2
 st_status st_fdm_solve(st_fdm* h, const void* F, const void* psi0, void* psi,
                        const st_solve_opts* opts, st_solve_info* info, void* stream);
 
+/* Bartels-Stewart solve in FP64 (Section 3, step 1 with the Schur choice, eq. LGS_x): with
+ * (i B_t)^{-1} M_t = Z T Z^H (Z unitary, T upper triangular), Psi_hat = Z W and G = Z^H (i B_t)^{-1} F~,
+ *     (M_x + T_ll A_x) w_l = g_l - A_x sum_{k>l} T_lk w_k,   l = n_t - 1, ..., 0.
+ * The n_t spatial matrices are factorised together (the FDM's spatial solver, factors kept), then the
+ * coupled solves run one after another.  Z is perfectly conditioned, so the result does not carry the
+ * rounding of kappa_2(X_t); the solves are sequential in l.  The Schur transforms are set up on the
+ * first call (host FP64, O(n_t^3)).  F, psi0 (may be NULL), psi: device c128 as in st_fdm_solve; psi
+ * must not alias F.  Needs memory for all n_t FP64 factors.  Errors: ST_ERR_ARG, ST_ERR_OOM,
+ * ST_ERR_CUDA, ST_ERR_ZERO_PIVOT (when info is non-NULL; the call then synchronises). */
+st_status st_bs_solve(st_fdm* h, const void* F, const void* psi0, void* psi, st_solve_info* info, void* stream);
+
 /* FP64 Kronecker residual R = F~ - K (psi - 1 (x) psi0) with F~ = F - m_t (x) A_x psi0
  * (eq. LGS; c128 arrays, psi0 may be NULL).  R may be NULL (norm only); it may alias F but not psi
  * or psi0 (ST_ERR_ARG).  rel_norm (host, may be

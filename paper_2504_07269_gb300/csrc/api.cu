@@ -9,6 +9,7 @@
 #include <cstring>
 #include <new>
 #include <string>
+#include <thread>
 #include <vector>
 
 #include "device.cuh"
@@ -38,6 +39,7 @@ cudaError_t launch_multiaxpy(const double2* const* Vdev, int nv, const double2* 
                              cudaStream_t st);
 cudaError_t launch_scale(const double2* x, double alpha, double2* y, size_t n, cudaStream_t st);
 cudaError_t launch_set_scalars(double* dst, double a, double b, cudaStream_t st);
+cudaError_t launch_bs_accum(int n_t, int n_x, int l, const double2* T, double2* W, cudaStream_t st);
 int krylov_partial_count();
 int krylov_max_vectors();
 
@@ -153,6 +155,12 @@ void free_handle(st_fdm* h) {
     cudaFree(h->mf_csrv);
     cudaFree(h->mf_upd);
     cudaFree(h->mf_uvec);
+    cudaFree(h->bs_Z);
+    cudaFree(h->bs_Y);
+    cudaFree(h->bs_T);
+    cudaFree(h->bs_shift);
+    cudaFree(h->bs_Ym);
+    cudaFree(h->bs_w);
     delete h;
 }
 
@@ -233,6 +241,11 @@ template <>
 const double2* shifts_of<double>(const st_fdm* h) { return h->s64; }
 template <>
 const float2* shifts_of<float>(const st_fdm* h) { return h->s32; }
+// the shifts of the factorisations: the eigenvalues s_k, or (FP64, Bartels-Stewart) the Schur diagonal
+template <typename T>
+const C<T>* active_shifts(const st_fdm* h) { return shifts_of<T>(h); }
+template <>
+const double2* active_shifts<double>(const st_fdm* h) { return h->shift_override ? h->shift_override : h->s64; }
 
 // Partial keep when not all complex64 factors fit: the number of leading systems whose factors
 // stay in memory (partial_keep_systems), with one wave of transient factors (one system per
@@ -289,11 +302,15 @@ bool mf_factors_fit(st_fdm* h, size_t elem) {
 }
 
 template <typename T>
+MfArgs<T> mf_args(const st_fdm* h, C<T>* G);
+template <typename T>
+cudaError_t mf_levels(const st_fdm* h, MfArgs<T>& a, int k0, int cnt, int what, cudaStream_t st);
+
+template <typename T>
 st_status mf_run(st_fdm* h, C<T>* G, int mode, cudaStream_t st) {
     const MfPlan& P = h->mf;
     const int n_t = h->tm.n_t;
     const size_t esz = sizeof(C<T>);
-    const int H = (int)P.level_ptr.size() - 1;
     if (mode == 2 && (!h->factors_valid || h->factors_prec != (int)esz))
         return fail(ST_ERR_ARG, "spatial solve: no stored factors");
     size_t freeb = 0, total = 0;
@@ -325,6 +342,25 @@ st_status mf_run(st_fdm* h, C<T>* G, int mode, cudaStream_t st) {
         s = grow(h->ws_L, h->ws_L_bytes, (size_t)kc * P.factor_entries * esz, "factors");
     }
     if (s != ST_OK) return s;
+    MfArgs<T> a = mf_args<T>(h, G);
+    a.fac_keep = (mode == 0) ? 0 : 1;
+    auto levels = [&](int k0, int cnt, int what) -> cudaError_t { return mf_levels<T>(h, a, k0, cnt, what, st); };
+    for (int k0 = 0; k0 < n_t; k0 += (int)kc) {
+        const int cnt = (int)std::min<long long>(kc, n_t - k0);
+        if (mode != 2) CUDA_TRY(levels(k0, cnt, 0));
+        CUDA_TRY(levels(k0, cnt, 1));
+        CUDA_TRY(levels(k0, cnt, 2));
+    }
+    if (mode == 1) {
+        h->factors_valid = 1;
+        h->factors_prec = (int)esz;
+    }
+    return ST_OK;
+}
+
+template <typename T>
+MfArgs<T> mf_args(const st_fdm* h, C<T>* G) {
+    const MfPlan& P = h->mf;
     MfArgs<T> a;
     a.fronts = h->mf_fronts;
     a.level_fronts = h->mf_level;
@@ -343,10 +379,11 @@ st_status mf_run(st_fdm* h, C<T>* G, int mode, cudaStream_t st) {
         a.Mv = h->mf_csrv;
         a.Av = h->mf_csrv + h->mf_csrv_nnz;
     }
-    a.shifts = shifts_of<T>(h);
+    a.shifts = active_shifts<T>(h);
     a.fac = reinterpret_cast<C<T>*>(h->ws_L);
     a.fac_stride = P.factor_entries;
-    a.fac_keep = (mode == 0) ? 0 : 1;
+    a.fac_keep = 1;
+    a.k0 = 0;
     a.upd = reinterpret_cast<C<T>*>(h->mf_upd);
     a.upd_stride = P.update_entries;
     a.uvec = reinterpret_cast<C<T>*>(h->mf_uvec);
@@ -354,7 +391,15 @@ st_status mf_run(st_fdm* h, C<T>* G, int mode, cudaStream_t st) {
     a.rhs = G;
     a.n = h->sm.n_x;
     a.status = h->ws_status;
-    auto levels = [&](int k0, int cnt, int what) -> cudaError_t {
+    return a;
+}
+
+// what: 0 = factorise, 1 = forward substitution, 2 = backward substitution, systems k0 .. k0 + cnt - 1
+template <typename T>
+cudaError_t mf_levels(const st_fdm* h, MfArgs<T>& a, int k0, int cnt, int what, cudaStream_t st) {
+    const MfPlan& P = h->mf;
+    const int H = (int)P.level_ptr.size() - 1;
+    {
         a.k0 = k0;
         if (what == 0) {
             for (int l = 0; l < H; ++l) {
@@ -375,18 +420,30 @@ st_status mf_run(st_fdm* h, C<T>* G, int mode, cudaStream_t st) {
             }
         }
         return cudaSuccess;
-    };
-    for (int k0 = 0; k0 < n_t; k0 += (int)kc) {
-        const int cnt = (int)std::min<long long>(kc, n_t - k0);
-        if (mode != 2) CUDA_TRY(levels(k0, cnt, 0));
-        CUDA_TRY(levels(k0, cnt, 1));
-        CUDA_TRY(levels(k0, cnt, 2));
     }
-    if (mode == 1) {
-        h->factors_valid = 1;
-        h->factors_prec = (int)esz;
-    }
-    return ST_OK;
+}
+
+// the launch arguments common to every banded kernel of a handle (windows and factor storage unset)
+template <typename T>
+BandArgs<T> band_args(const st_fdm* h, C<T>* G) {
+    const SpaceMats& sm = h->sm;
+    BandArgs<T> a;
+    a.n = sm.n_x;
+    a.m = sm.m;
+    a.b = sm.m + 1;
+    a.n_sys = h->tm.n_t;
+    a.k0 = 0;
+    a.Mc = (T)sm.Mc; a.Mw = (T)sm.Mw; a.Ms = (T)sm.Ms; a.Md = (T)sm.Md;
+    a.Ac = (T)sm.Ac; a.Aw = (T)sm.Aw; a.As = (T)sm.As; a.Ad = (T)sm.Ad;
+    a.shifts = active_shifts<T>(h);
+    a.rhs = G;
+    a.win = nullptr;
+    a.L = nullptr;
+    a.D = nullptr;
+    a.keep = 0;
+    a.status = h->ws_status;
+    a.probe_ns = h->wait_probe_ns;
+    return a;
 }
 
 // mode: 0 = factor and solve (factors transient, in chunks of systems), 1 = factor, keep all
@@ -407,18 +464,7 @@ st_status band_run(st_fdm* h, C<T>* G, int mode, cudaStream_t st) {
     int occ = band_occupancy<T>(nb, b);
     if (occ < 1) occ = 1;
     const int grid = std::max(1, std::min(n_t, occ * h->sm_count));
-    BandArgs<T> a;
-    a.n = n;
-    a.m = sm.m;
-    a.b = b;
-    a.n_sys = n_t;
-    a.k0 = 0;
-    a.Mc = (T)sm.Mc; a.Mw = (T)sm.Mw; a.Ms = (T)sm.Ms; a.Md = (T)sm.Md;
-    a.Ac = (T)sm.Ac; a.Aw = (T)sm.Aw; a.As = (T)sm.As; a.Ad = (T)sm.Ad;
-    a.shifts = shifts_of<T>(h);
-    a.rhs = G;
-    a.status = h->ws_status;
-    a.probe_ns = h->wait_probe_ns;
+    BandArgs<T> a = band_args<T>(h, G);
     const int nbw = nb == 64 ? 32 : (nb < 0 ? -nb : nb);   // panel width of the selected kernel
     const size_t WR = (size_t)b + nbw;
     if (mode == 3 || mode == 4) {
@@ -932,6 +978,118 @@ st_status adjoint_direct(st_fdm* h, bool fp32, const void* G, void* lambda, cuda
     return xform32(h, XF_YT, H, false, nullptr, 0, lambda, false, 1, 0, nullptr, nullptr, nullptr, nullptr, st);
 }
 
+// ------------------------------------------------------------------ Bartels-Stewart (FP64)
+// The Schur choice of step 1 (Section 3): (i B_t)^{-1} M_t = Z T Z^H with Z unitary and T upper
+// triangular, so that with Psi_hat = Z W and G = Z^H (i B_t)^{-1} F~ the spatial problems of eq. LGS_x
+// couple through T:
+//     (M_x + T_ll A_x) w_l = g_l - A_x sum_{k > l} T_lk w_k,     l = n_t - 1, ..., 0.
+// All n_t spatial matrices are factorised at once (the FDM's kernels, at the shifts T_ll, factors
+// kept); the coupled solves then run one system at a time from the last, each followed by a rank-one
+// update of the couplings of all earlier rows.  A reference path: robust where X_t is
+// ill-conditioned, with no time parallelism in its solves.
+st_status bs_prepare(st_fdm* h) {
+    if (h->bs_Z) return ST_OK;
+    const int n = h->tm.n_t;
+    const TimeDecomp& td = h->td;
+    if (td.Zs.size() != (size_t)n * n || td.Ts.size() != (size_t)n * n || td.Binv.size() != (size_t)n * n)
+        return fail(ST_ERR_ARG, "Bartels-Stewart: no Schur form");
+    std::vector<cd> Z((size_t)n * n), T((size_t)n * n, cd(0.0)), Y((size_t)n * n), sh(n), ym(n, cd(0.0));
+    for (int i = 0; i < n; ++i)
+        for (int j = 0; j < n; ++j) {
+            Z[(size_t)i * n + j] = td.Zs[i + (size_t)j * n];
+            if (i <= j) T[(size_t)i * n + j] = td.Ts[i + (size_t)j * n];
+        }
+    for (int i = 0; i < n; ++i) sh[i] = td.Ts[i + (size_t)i * n];
+    // Y = Z^H (i B_t)^{-1} = Z^H (-i B_t^{-1})
+    {
+        const int nth = std::max(1, std::min<int>(16, (int)std::thread::hardware_concurrency()));
+        std::vector<std::thread> pool;
+        for (int t = 0; t < nth; ++t)
+            pool.emplace_back([&, t]() {
+                for (int i = t; i < n; i += nth)
+                    for (int j = 0; j < n; ++j) {
+                        cd acc = 0.0;
+                        for (int k = 0; k < n; ++k) acc += std::conj(td.Zs[k + (size_t)i * n]) * td.Binv[k + (size_t)j * n];
+                        Y[(size_t)i * n + j] = cd(0.0, -1.0) * acc;
+                    }
+            });
+        for (auto& th : pool) th.join();
+    }
+    for (int i = 0; i < n; ++i)
+        for (int k = 0; k < n; ++k) ym[i] += Y[(size_t)i * n + k] * h->tm.m[k];
+    st_status s = upload(&h->bs_Z, Z.data(), Z.size() * sizeof(double2), "Schur Z");
+    if (s == ST_OK) s = upload(&h->bs_Y, Y.data(), Y.size() * sizeof(double2), "Schur Y");
+    if (s == ST_OK) s = upload(&h->bs_T, T.data(), T.size() * sizeof(double2), "Schur T");
+    if (s == ST_OK) s = upload(&h->bs_shift, sh.data(), sh.size() * sizeof(double2), "Schur shifts");
+    if (s == ST_OK) s = upload(&h->bs_Ym, ym.data(), ym.size() * sizeof(double2), "Schur Y m_t");
+    if (s != ST_OK) {
+        cudaFree(h->bs_Z);
+        h->bs_Z = nullptr;
+    }
+    return s;
+}
+
+// w_l = C_l^{-1} w_l with the kept FP64 factors of system l (row l of W)
+st_status bs_solve_one(st_fdm* h, double2* W, int l, cudaStream_t st) {
+    if (h->spatial == 1) {
+        MfArgs<double> a = mf_args<double>(h, W);
+        a.fac_keep = 1;
+        CUDA_TRY(mf_levels<double>(h, a, l, 1, 1, st));
+        CUDA_TRY(mf_levels<double>(h, a, l, 1, 2, st));
+        return ST_OK;
+    }
+    BandArgs<double> a = band_args<double>(h, W);
+    a.L = reinterpret_cast<double2*>(h->ws_L);
+    a.D = reinterpret_cast<double2*>(h->ws_D);
+    a.keep = 1;
+    CUDA_TRY(subst_launch<double>(a, l, 1, true, st));
+    CUDA_TRY(subst_launch<double>(a, l, 1, false, st));
+    return ST_OK;
+}
+
+st_status bs_solve(st_fdm* h, const void* F, const void* psi0, void* psi, cudaStream_t st) {
+    const int n_t = h->tm.n_t, n_x = h->sm.n_x;
+    const size_t N = (size_t)n_t * n_x;
+    release_refinement_workspace(h);
+    st_status s = bs_prepare(h);
+    if (s == ST_OK) s = ensure_common(h);
+    if (s == ST_OK) s = grow(h->ws_big, h->ws_big_bytes, N * sizeof(double2), "G");
+    if (s == ST_OK) s = grow(h->bs_w, h->bs_w_bytes, N * sizeof(double2), "Bartels-Stewart W");
+    if (s != ST_OK) return s;
+    double2* G = reinterpret_cast<double2*>(h->ws_big);
+    double2* W = reinterpret_cast<double2*>(h->bs_w);
+    double2* tmp = vec_slot(h, 2);
+    double2* apsi0 = nullptr;
+    if (psi0) {
+        apsi0 = vec_slot(h, 0);
+        CUDA_TRY(launch_stencil_A(h->sm, psi0, false, nullptr, 1.0, apsi0, st));
+    }
+    s = xform<double, double, double, double>(reinterpret_cast<double*>(h->bs_Y), n_t, n_x, F, G, 0, 0, 0, nullptr,
+                                              nullptr, nullptr, psi0 ? h->bs_Ym : nullptr, apsi0, st);
+    if (s != ST_OK) return s;
+    // factorise every C_l = M_x + T_ll A_x into kept storage (on zero right-hand sides)
+    CUDA_TRY(cudaMemsetAsync(W, 0, N * sizeof(double2), st));
+    h->shift_override = h->bs_shift;
+    s = band_run<double>(h, W, 1, st);
+    h->shift_override = nullptr;
+    if (s == ST_OK) {
+        CUDA_TRY(cudaMemsetAsync(W, 0, N * sizeof(double2), st));
+        for (int l = n_t - 1; l >= 0 && s == ST_OK; --l) {
+            double2* wl = W + (size_t)l * n_x;
+            // right-hand side g_l - A_x (sum_{k>l} T_lk w_k), the sum accumulated in row l
+            CUDA_TRY(launch_stencil_A(h->sm, wl, false, G + (size_t)l * n_x, -1.0, tmp, st));
+            CUDA_TRY(cudaMemcpyAsync(wl, tmp, (size_t)n_x * sizeof(double2), cudaMemcpyDeviceToDevice, st));
+            s = bs_solve_one(h, W, l, st);
+            if (s == ST_OK) CUDA_TRY(launch_bs_accum(n_t, n_x, l, h->bs_T, W, st));
+        }
+    }
+    // the kept factors belong to the Schur shifts, not to the eigenvalues of the FDM
+    h->factors_valid = 0;
+    if (s != ST_OK) return s;
+    return xform<double, double, double, double>(reinterpret_cast<double*>(h->bs_Z), n_t, n_x, W, psi, 0, 0, 0, nullptr,
+                                                 nullptr, psi0, nullptr, nullptr, st);
+}
+
 st_status validate_opts(const st_solve_opts* o, st_solve_opts& out) {
     st_solve_opts d;
     std::memset(&d, 0, sizeof(d));
@@ -1285,6 +1443,28 @@ extern "C" st_status st_adjoint_lift(st_fdm* h, const void* grad_psi, const void
                             reinterpret_cast<const double2*>(grad_F), h->dt.m, s1, s2, st));
     CUDA_TRY(launch_stencil_A(h->sm, s2, false, s1, -1.0, reinterpret_cast<double2*>(grad_psi0), st));
     return ST_OK;
+}
+
+extern "C" st_status st_bs_solve(st_fdm* h, const void* F, const void* psi0, void* psi, st_solve_info* info,
+                                 void* stream) {
+    if (!h || !F || !psi) return fail(ST_ERR_ARG, "st_bs_solve: NULL argument");
+    if (F == psi) return fail(ST_ERR_ARG, "st_bs_solve: psi must not alias F");
+    const long long l0 = launches_issued();
+    DeviceGuard g(h->device);
+    cudaStream_t st = S(stream);
+    fill_info_common(h, info, ST_FP64);
+    CUDA_TRY(cudaMemsetAsync(h->ws_status, 0, 2 * sizeof(int), st));
+    st_status s = bs_solve(h, F, psi0, psi, st);
+    if (s == ST_OK && info) {
+        info->sweeps = 1;
+        info->factors_kept = 1;
+        info->kept_systems = h->tm.n_t;
+        info->rel_residual = -1;
+        for (int i = 0; i < 16; ++i) info->residual_history[i] = -1;
+        s = check_status_flag(h, st);
+    }
+    if (info) info->kernel_launches = (int)(launches_issued() - l0);
+    return s;
 }
 
 extern "C" st_status st_time_transform(st_fdm* h, int which, int precision, const void* in, void* out, void* stream) {

@@ -304,4 +304,13 @@ struct st_fdm {
     size_t mf_upd_bytes = 0;
     void* mf_uvec = nullptr;      // update vectors for a chunk of systems
     size_t mf_uvec_bytes = 0;
+    // Bartels-Stewart (Schur choice of step 1; FP64 reference path), set up at its first use
+    double2* bs_Z = nullptr;      // Z (row-major n_t x n_t): back transform
+    double2* bs_Y = nullptr;      // Z^H (i B_t)^{-1}: forward transform
+    double2* bs_T = nullptr;      // Schur form T (row-major, upper triangular)
+    double2* bs_shift = nullptr;  // T_ll, the shifts of the spatial systems in Schur order
+    double2* bs_Ym = nullptr;     // bs_Y m_t (lifting)
+    void* bs_w = nullptr;         // (n_t, n_x): accumulated couplings, then the solved w_l
+    size_t bs_w_bytes = 0;
+    const double2* shift_override = nullptr;   // FP64 factorisations use these shifts when set
 };

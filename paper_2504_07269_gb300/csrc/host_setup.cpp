@@ -49,6 +49,8 @@ st_status time_decompose(const TimeMats& tm, int threads, TimeDecomp& out) {
     std::vector<cd> Z((size_t)n * n);
     if (!la::complex_schur(n, A.data(), Z.data(), threads))
         return fail(ST_ERR_NOT_CONVERGED, "time decomposition: QR iteration did not converge");
+    out.Zs = Z;
+    out.Ts = A;
     std::vector<cd> Xc((size_t)n * n);
     la::schur_eigenvectors(n, A.data(), Z.data(), Xc.data(), threads);
     std::vector<cd> s(n);
@@ -80,6 +82,7 @@ st_status time_decompose(const TimeMats& tm, int threads, TimeDecomp& out) {
             out.X[(size_t)i * n + j] = X[i + (size_t)j * n];
             out.Y[(size_t)i * n + j] = Yc[i + (size_t)j * n];
         }
+    out.Binv = std::move(Binv);
     double mn = 1e300;
     for (int k = 0; k < n; ++k) mn = std::min(mn, -out.s[k].imag());
     out.min_neg_im = mn;

@@ -114,6 +114,10 @@ struct TimeDecomp {
     std::vector<cd> Y;   // row-major, Y = X^{-1} (i B)^{-1}
     double kappa = 0;
     double min_neg_im = 0;
+    // the complex Schur form behind the eigen-decomposition, (i B_t)^{-1} M_t = Z T Z^H (column-major),
+    // and B_t^{-1} (column-major): the Bartels-Stewart solver's step 1
+    std::vector<cd> Zs, Ts;
+    std::vector<double> Binv;
 };
 
 st_status time_decompose(const TimeMats& tm, int threads, TimeDecomp& out);

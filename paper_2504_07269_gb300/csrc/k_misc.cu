@@ -253,6 +253,26 @@ __global__ void k_colsums(int n_t, int n_x, const double2* U1, const double2* U2
     out2[x] = b;
 }
 
+// Bartels-Stewart coupling (eq. LGS_x, Schur choice): once w_l is solved, every earlier row
+// r < l of the accumulator gains T[r, l] w_l (T row-major n_t x n_t, upper triangular).
+__global__ void k_bs_accum(int n_t, int n_x, int l, const double2* T, double2* W) {
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    const int r = blockIdx.y;
+    if (x >= n_x || r >= l) return;
+    const double2 t = T[(size_t)r * n_t + l];
+    const double2 w = W[(size_t)l * n_x + x];
+    double2& a = W[(size_t)r * n_x + x];
+    a.x += t.x * w.x - t.y * w.y;
+    a.y += t.x * w.y + t.y * w.x;
+}
+
+cudaError_t launch_bs_accum(int n_t, int n_x, int l, const double2* T, double2* W, cudaStream_t st) {
+    if (l <= 0) return cudaSuccess;
+    k_bs_accum<<<dim3((n_x + 255) / 256, l), 256, 0, st>>>(n_t, n_x, l, T, W);
+    note_launches(1);
+    return cudaGetLastError();
+}
+
 // ------------------------------------------------------------------ launchers
 static Stencil make_stencil(const SpaceMats& sm) {
     return Stencil{sm.m, sm.Mc, sm.Mw, sm.Ms, sm.Md, sm.Ac, sm.Aw, sm.As, sm.Ad};

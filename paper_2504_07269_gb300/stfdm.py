@@ -258,6 +258,20 @@ def st_fdm_solve(h: FdmHandle, F, psi0=None, psi=None, precision="fp64", tol=0.0
     return psi, (_info_dict(info) if want_info else None)
 
 
+def st_bs_solve(h: FdmHandle, F, psi0=None, psi=None, stream=None, want_info=True):
+    """FP64 Bartels-Stewart solve (Schur choice of step 1): same arrays as st_fdm_solve(fp64)."""
+    _check_st(h, F, torch.complex128, "F")
+    _check_vec(h, psi0, torch.complex128, "psi0")
+    if psi is None:
+        psi = torch.empty_like(F)
+    _check_st(h, psi, torch.complex128, "psi")
+    info = _lib.st_solve_info()
+    st = lib().st_bs_solve(h.ptr, _ptr(F), _ptr(psi0), _ptr(psi), ctypes.byref(info) if want_info else None,
+                           _stream(stream))
+    _check_with_info(st, "st_bs_solve", info if want_info else None)
+    return psi, (_info_dict(info) if want_info else None)
+
+
 def st_residual(h: FdmHandle, F, psi0, psi, R=None, want_norm=True, stream=None):
     _check_st(h, F, torch.complex128, "F")
     _check_st(h, psi, torch.complex128, "psi")
