@@ -267,10 +267,19 @@ def run_reference(args):
 # 1e-12 sits at the FP64 residual floor (the GMRES estimate reaches 5e-13 while the true residual is
 # 1.2e-12) and costs a second restart cycle.
 SINGLE_TOL = {"c3": 1e-10, "c2": 1e-11}
+# Error target of the single-problem mixed solve (the library's error estimate ||FDM32(R)|| / ||psi_hat||,
+# checked each time the residual target is met).  At 384^2/P2-1024 a residual of 2e-11 still leaves an
+# error of 1e-8 against the FP64 references (the error/residual ratio approaches cond(K)), so the residual
+# target alone does not give the metric's 1e-9; the estimate keeps the iteration going until it does.
+SINGLE_ERR_TOL = {"c3": 2e-10}
 
 
 def single_tol(pr):
     return SINGLE_TOL.get(pr.name, 1e-11)
+
+
+def single_err_tol(pr):
+    return SINGLE_ERR_TOL.get(pr.name, 0.0)
 
 
 def _config(pr, args):
@@ -280,7 +289,7 @@ def _config(pr, args):
     return {"workload": f"{pr.n}x{pr.n} squares P1 space ({pr.n_x} nodes), P{pr.p_t} time {len(pr.t_nodes) - 1} "
                         f"uniform elements (n_t={pr.n_t}), T={pr.t_nodes[-1]:g}; {pr.unknowns} unknowns; {inputs}",
             "name": pr.name, "precision": args.precision, "spatial_solver": getattr(args, "spatial", "banded"),
-            "tol": single_tol(pr), "n_x": pr.n_x, "n_t": pr.n_t,
+            "tol": single_tol(pr), "err_tol": single_err_tol(pr), "n_x": pr.n_x, "n_t": pr.n_t,
             "unknowns": pr.unknowns, "l2_flush": f"inputs ({gb:.2f} GB c128 load) larger than the 129 MB L2",
             "parallelism": "replicas" if args.gpus > 1 else "single GPU"}
 
@@ -300,6 +309,7 @@ def run_ours(args):
 
     pr = synth.config_problem(args.config)
     tol = single_tol(pr)
+    etol = single_err_tol(pr)
     t0 = time.perf_counter()
     h = stfdm.setup_problem(pr.n, pr.p_t, pr.t_nodes, Lx=pr.Lx, Ly=pr.Ly, device=local, spatial_solver=args.spatial)
     setup_s = time.perf_counter() - t0
@@ -316,7 +326,7 @@ def run_ours(args):
             print(json.dumps({"profile_xform": args.config, "norm": float(torch.linalg.vector_norm(G32))}))
         return 0
     if args.profile_step:
-        _, info = stfdm.st_fdm_solve(h, F, p0, psi=psi, precision=args.precision, tol=tol)
+        _, info = stfdm.st_fdm_solve(h, F, p0, psi=psi, precision=args.precision, tol=tol, err_tol=etol)
         torch.cuda.synchronize()
         if rank == 0:
             print(json.dumps({"profile_step": args.config, "precision": args.precision, "info": info}))
@@ -338,7 +348,7 @@ def run_ours(args):
         Fd.copy_(Fh, non_blocking=True)
         p0d.copy_(p0h, non_blocking=True)
         ev[1].record()
-        _, info = stfdm.st_fdm_solve(h, Fd, p0d, psi=psi, precision=args.precision, tol=tol)
+        _, info = stfdm.st_fdm_solve(h, Fd, p0d, psi=psi, precision=args.precision, tol=tol, err_tol=etol)
         ev[2].record()
         psih.copy_(psi, non_blocking=True)
         ev[3].record()
@@ -366,6 +376,8 @@ def run_ours(args):
     t_ms = reduce_max(statistics.mean(solve_ms), world, dev)
     e2e_ms = reduce_max(statistics.mean(step_ms), world, dev)
     value = world * pr.unknowns / (t_ms * 1e-3)
+    print(f"timed: solve {t_ms:.1f} ms, step {e2e_ms:.1f} ms, {value:.4e} unknowns/s, info {info}", file=sys.stderr,
+          flush=True)
     sweeps = int(info.get("sweeps", 1)) if info else 1
     # our kernels per step: the library counts the launches each solve issues (an ncu launch list of
     # one step agrees with it); the copies are not kernels
@@ -373,7 +385,7 @@ def run_ours(args):
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
 
     # ---- error against the FP64 FDM on the same inputs, and against a tightly refined solution
-    err = err_tight = fp64_res = None
+    err = err_tight = fp64_res = tight_res = None
     fp64_value = None
     fp32_value = fp32_err = None
     if not args.no_fp64_check and args.precision != "fp64":
@@ -405,8 +417,13 @@ def run_ours(args):
         fp64_res = float(stfdm.st_residual(h, F64, p064, ref)[0])
         # the FP64 FDM carries the rounding of X_t (about kappa_2(X_t) eps in the residual): a solution
         # refined to 1e-13 says which of the two is off
-        stfdm.st_fdm_solve(h, F64, p064, psi=ref, precision="mixed", tol=1e-13, max_sweeps=80, want_info=False)
+        try:
+            stfdm.st_fdm_solve(h, F64, p064, psi=ref, precision="mixed", tol=1e-12, err_tol=1e-12, max_sweeps=60,
+                               want_info=False)
+        except Exception as ex:   # at the FP64 floor: the iterate is still the tightest reference at hand
+            print(f"tight reference: {ex}", file=sys.stderr)
         err_tight = float(torch.linalg.vector_norm(mine - ref) / torch.linalg.vector_norm(ref))
+        tight_res = float(stfdm.st_residual(h, F64, p064, ref)[0])
         del ref, mine, F64, p064
         torch.cuda.empty_cache()
 
@@ -466,7 +483,9 @@ def run_ours(args):
                 "data": ("synthetic (seeded Gaussian packets, f = 0)" if pr.name == "c3"
                          else "synthetic (manufactured solution, interpolated load)"),
                 "config": _config(pr, args),
-                "err_vs_fp64": err, "fp64_fdm_rel_residual": fp64_res, "err_vs_refined_1e-13": err_tight,
+                "err_vs_fp64": err, "fp64_fdm_rel_residual": fp64_res, "err_vs_tight": err_tight,
+                "tight_rel_residual": tight_res,
+                "err_estimate": info.get("rel_error_estimate") if info else None,
                 "fp64_fdm_unknowns_per_s": fp64_value,
                 "fp32_fdm_unknowns_per_s": fp32_value, "fp32_fdm_err_vs_fp64": fp32_err, "sweeps": sweeps,
                 "restart": info.get("restart") if info else None,

@@ -102,6 +102,11 @@ typedef struct {
                            host synchronisation (no convergence test; the final residual is reported
                            when info is non-NULL) */
     int method;         /* ST_MIXED: ST_REFINE_GMRES (default) or ST_REFINE_CLASSIC */
+    double err_tol;     /* ST_MIXED with GMRES: > 0 also requires the error estimate ||FDM32(R)|| / ||psi_hat||
+                           (one extra FP32 application each time the residual target is met) to be
+                           <= err_tol; while it is not, the residual target is lowered and the
+                           iteration continues.  A small residual does not bound the error by itself:
+                           the error can reach cond(K) times the residual.  <= 0: off */
 } st_solve_opts;
 
 /* refinement methods of ST_MIXED.  Both compute the residual in FP64 and correct with the
@@ -124,6 +129,7 @@ typedef struct {
     int tensor_cores;            /* 1 if the complex-FP32 time transforms ran on the tcgen05 tensor cores */
     int kernel_launches;         /* kernels this call launched (st_fdm_solve, st_adjoint_solve; 0 in batched solves) */
     int restart;                 /* ST_MIXED with GMRES: the restart length m used (0 otherwise) */
+    double rel_error_estimate;   /* ST_MIXED with GMRES and err_tol > 0: the last ||FDM32(R)|| / ||psi_hat|| (-1 otherwise) */
     int kept_systems;            /* ST_MIXED: spatial systems whose factors stayed in memory across
                                     applications (n_t when all were kept, 0 when none) */
 } st_solve_info;
@@ -132,7 +138,7 @@ typedef struct {
 const char* st_status_string(st_status s);
 const char* st_last_error_message(void);
 int st_abi_version(void);   /* returns STFDM_ABI_VERSION of the built library */
-#define STFDM_ABI_VERSION 6
+#define STFDM_ABI_VERSION 7
 
 /* ------------------------------------------------------------------ assembly (host) */
 /* Temporal matrices of eq. (matrix_t), Section 3.  p_t in {1, 2}: continuous piecewise

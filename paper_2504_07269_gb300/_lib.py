@@ -50,14 +50,14 @@ class st_setup_opts(ctypes.Structure):
 
 class st_solve_opts(ctypes.Structure):
     _fields_ = [("precision", c_int), ("tol", c_double), ("max_sweeps", c_int), ("keep_factors", c_int),
-                ("fixed_sweeps", c_int), ("method", c_int)]
+                ("fixed_sweeps", c_int), ("method", c_int), ("err_tol", c_double)]
 
 
 class st_solve_info(ctypes.Structure):
     _fields_ = [("sweeps", c_int), ("factors_kept", c_int), ("rel_residual", c_double),
                 ("residual_history", c_double * 16), ("kappa_x", c_double), ("min_neg_im_shift", c_double),
                 ("setup_seconds", c_double), ("tensor_cores", c_int), ("kernel_launches", c_int),
-                ("restart", c_int), ("kept_systems", c_int)]
+                ("restart", c_int), ("rel_error_estimate", c_double), ("kept_systems", c_int)]
 
 
 class st_batch_opts(ctypes.Structure):

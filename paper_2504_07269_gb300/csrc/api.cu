@@ -844,10 +844,13 @@ st_status solve_mixed_gmres(st_fdm* h, bool adjoint, const void* F, const void* 
     CUDA_TRY(cudaMemsetAsync(psi, 0, N * sizeof(double2), st));
     CUDA_TRY(cudaMemsetAsync(h->ws_status, 0, 2 * sizeof(int), st));
     double2* x = reinterpret_cast<double2*>(psi);
+    // the iterate's pointer after the basis, for its norm in the error estimate
+    CUDA_TRY(cudaMemcpyAsync(const_cast<double2**>(P) + 2 * m + 2, &x, sizeof(double2*), cudaMemcpyHostToDevice, st));
     double hist[16];
     int nh = 0;
     int its = 0;
-    double bnorm = -1, rel = -1;
+    double bnorm = -1, rel = -1, err_est = -1;
+    double cur_tol = tol;
     bool converged = false, first = true, x_zero = true;
     std::vector<cd> H((size_t)(m + 1) * m), g(m + 1), sn(m);
     std::vector<double> cs(m);
@@ -863,9 +866,30 @@ st_status solve_mixed_gmres(st_fdm* h, bool adjoint, const void* F, const void* 
         rel = bnorm > 0 ? beta / bnorm : 0.0;
         if (nh < 15) hist[nh++] = rel;
         if (!std::isfinite(rel)) return fail(ST_ERR_NOT_CONVERGED, "refinement: non-finite residual");
-        if (rel <= tol || beta == 0.0) {
-            converged = true;
-            break;
+        if (rel <= cur_tol || beta == 0.0) {
+            if (!(o.err_tol > 0) || beta == 0.0) {
+                converged = true;
+                break;
+            }
+            if (its >= maxit) break;
+            // error estimate: the FP32 FDM of the residual, relative to the iterate
+            CUDA_TRY(launch_scale(w, 1.0 / beta, Vp(0), N, st));
+            s = precond32(h, adjoint, Vp(0), Zp(0), keep, first, scal + 4, st);
+            if (s != ST_OK) return s;
+            ++its;
+            CUDA_TRY(launch_multidot(P + m + 1, 1, Zp(0), N, partial, hb, st));
+            CUDA_TRY(launch_multidot(P + 2 * m + 2, 1, x, N, partial, hb + MV, st));
+            CUDA_TRY(cudaMemcpyAsync(hh.data(), hb, 2 * MV * sizeof(double2), cudaMemcpyDeviceToHost, st));
+            CUDA_TRY(cudaStreamSynchronize(st));
+            const double zz = std::max(0.0, hh[0].x), xx = std::max(0.0, hh[MV].x);
+            err_est = xx > 0 ? beta * std::sqrt(zz / xx) : HUGE_VAL;
+            if (err_est <= o.err_tol) {
+                converged = true;
+                break;
+            }
+            // lower the residual target by the factor the estimate is off, and keep iterating
+            cur_tol = std::max(1e-16, std::min(0.5 * rel, rel * (0.5 * o.err_tol / err_est)));
+            continue;
         }
         if (its >= maxit) break;
         CUDA_TRY(launch_scale(w, 1.0 / beta, Vp(0), N, st));
@@ -920,7 +944,7 @@ st_status solve_mixed_gmres(st_fdm* h, bool adjoint, const void* F, const void* 
             }
             jdone = j + 1;
             const double est = std::abs(g[j + 1]) / bnorm;
-            if (est <= 0.5 * tol || j == m - 1 || its >= maxit || hn <= 1e-300) break;
+            if (est <= 0.5 * cur_tol || j == m - 1 || its >= maxit || hn <= 1e-300) break;
             CUDA_TRY(launch_scale(w, 1.0 / hn, Vp(j + 1), N, st));
         }
         // y = R^{-1} g, x += Z y
@@ -943,6 +967,7 @@ st_status solve_mixed_gmres(st_fdm* h, bool adjoint, const void* F, const void* 
         info->factors_kept = keep ? 1 : (h->kept_sys > 0 ? 2 : 0);
         info->restart = m;
         info->kept_systems = keep ? n_t : h->kept_sys;
+        info->rel_error_estimate = err_est;
         info->rel_residual = rel;
         for (int i = 0; i < 16; ++i) info->residual_history[i] = (i < nh) ? hist[i] : -1.0;
     }
@@ -1111,6 +1136,7 @@ void fill_info_common(const st_fdm* h, st_solve_info* info, int precision) {
     info->tensor_cores = (precision != ST_FP64 && h->tc_ok) ? 1 : 0;
     info->restart = 0;
     info->kept_systems = 0;
+    info->rel_error_estimate = -1;
 }
 
 }  // namespace

@@ -119,11 +119,11 @@ def _dtype(precision):
 REFINE = {"gmres": _lib.ST_REFINE_GMRES, "classic": _lib.ST_REFINE_CLASSIC}
 
 
-def _opts(precision="fp64", tol=0.0, max_sweeps=0, keep_factors=-1, fixed_sweeps=0, method="gmres"):
+def _opts(precision="fp64", tol=0.0, max_sweeps=0, keep_factors=-1, fixed_sweeps=0, method="gmres", err_tol=0.0):
     if precision not in PREC:
         raise ValueError(f"unknown precision {precision!r}")
     return _lib.st_solve_opts(PREC[precision], float(tol), int(max_sweeps), int(keep_factors), int(fixed_sweeps),
-                              REFINE[method])
+                              REFINE[method], float(err_tol))
 
 
 def _info_dict(info: _lib.st_solve_info):
@@ -131,7 +131,7 @@ def _info_dict(info: _lib.st_solve_info):
                 residual_history=[v for v in info.residual_history if v >= 0], kappa_x=info.kappa_x,
                 min_neg_im_shift=info.min_neg_im_shift, setup_seconds=info.setup_seconds,
                 tensor_cores=info.tensor_cores, kernel_launches=info.kernel_launches, restart=info.restart,
-                kept_systems=info.kept_systems)
+                kept_systems=info.kept_systems, rel_error_estimate=info.rel_error_estimate)
 
 
 # ------------------------------------------------------------------ assembly / setup
@@ -243,14 +243,14 @@ def st_fdm_setup(t: TimeHandle, s: SpaceHandle, kappa_max: float = 0.0, device: 
 
 # ------------------------------------------------------------------ solves
 def st_fdm_solve(h: FdmHandle, F, psi0=None, psi=None, precision="fp64", tol=0.0, max_sweeps=0,
-                 keep_factors=-1, fixed_sweeps=0, stream=None, want_info=True, method="gmres"):
+                 keep_factors=-1, fixed_sweeps=0, stream=None, want_info=True, method="gmres", err_tol=0.0):
     dt = _dtype(precision)
     _check_st(h, F, dt, "F")
     _check_vec(h, psi0, dt, "psi0")
     if psi is None:
         psi = torch.empty_like(F)
     _check_st(h, psi, dt, "psi")
-    opts = _opts(precision, tol, max_sweeps, keep_factors, fixed_sweeps, method)
+    opts = _opts(precision, tol, max_sweeps, keep_factors, fixed_sweeps, method, err_tol)
     info = _lib.st_solve_info()
     st = lib().st_fdm_solve(h.ptr, _ptr(F), _ptr(psi0), _ptr(psi), ctypes.byref(opts),
                             ctypes.byref(info) if want_info else None, _stream(stream))
@@ -285,13 +285,13 @@ def st_residual(h: FdmHandle, F, psi0, psi, R=None, want_norm=True, stream=None)
 
 
 def st_adjoint_solve(h: FdmHandle, G, lam=None, precision="fp64", tol=0.0, max_sweeps=0, keep_factors=-1,
-                     fixed_sweeps=0, stream=None, want_info=True, method="gmres"):
+                     fixed_sweeps=0, stream=None, want_info=True, method="gmres", err_tol=0.0):
     dt = _dtype(precision)
     _check_st(h, G, dt, "G")
     if lam is None:
         lam = torch.empty_like(G)
     _check_st(h, lam, dt, "lambda")
-    opts = _opts(precision, tol, max_sweeps, keep_factors, fixed_sweeps, method)
+    opts = _opts(precision, tol, max_sweeps, keep_factors, fixed_sweeps, method, err_tol)
     info = _lib.st_solve_info()
     st = lib().st_adjoint_solve(h.ptr, _ptr(G), _ptr(lam), ctypes.byref(opts),
                                 ctypes.byref(info) if want_info else None, _stream(stream))

@@ -230,6 +230,7 @@ def config_problem(name: str) -> Problem:
     c3        384x384 squares, P2 time, 512 uniform elements, T=2 (150,209,536)
     c4        128x128 squares, P1 time, 256 uniform elements, T=1 (4,129,024)
     c2small   256x256 squares, P1 time, 16 uniform elements, T=1/32 (profiling case)
+    c3small   384x384 squares, P2 time, 8 uniform elements, T=1/32 (profiling case)
     paperJ    paper's level-J mesh: (32 2^J)^2 squares, P1, 64 2^J elements, T=5
     """
     if name == "c1":
@@ -242,6 +243,9 @@ def config_problem(name: str) -> Problem:
         return Problem(384, 2, uniform_time_nodes(512, 2.0), name=name, seed=3)
     if name == "c4":
         return Problem(128, 1, uniform_time_nodes(256, 1.0), name=name, seed=4)
+    if name == "c3small":
+        # the 384x384 spatial band of c3 with P2 time on 8 elements (n_t = 16): a small case for profiling
+        return Problem(384, 2, uniform_time_nodes(8, 2.0 / 64), name=name, seed=3)
     if name == "c2small":
         # the 256x256 spatial band of c2 with 16 time elements: a small case for profiling
         return Problem(256, 1, uniform_time_nodes(16, 1.0 / 32), name=name, seed=2)
