@@ -804,9 +804,11 @@ st_status solve_mixed_gmres(st_fdm* h, bool adjoint, const void* F, const void* 
         cudaMemGetInfo(&freeb, &total);
         size_t avail = freeb + h->ws_kry_bytes;
         if (keep) {
+            // the kept factors will take `fac` bytes, reusing what ws_L holds already
             const size_t fac = h->spatial == 1 ? (size_t)n_t * (size_t)h->mf.factor_entries * sizeof(float2)
                                                : (size_t)n_t * n_x * (size_t)(h->sm.m + 2) * sizeof(float2);
-            avail = avail > fac + h->ws_L_bytes ? avail - (fac > h->ws_L_bytes ? fac - h->ws_L_bytes : 0) : 0;
+            avail += h->ws_L_bytes + h->ws_D_bytes;
+            avail = avail > fac ? avail - fac : 0;
         }
         int grid = 0;
         size_t per = 0, fixed = 0;
@@ -1180,7 +1182,7 @@ st_status setup_spatial(st_fdm* h, int choice) {
     }
     if (s != ST_OK) return s;
     const MfPlan& P = h->mf;
-    if ((size_t)P.max_front * sizeof(double2) > h->smem_optin)
+    if (((size_t)P.max_front + 32 * 33) * sizeof(double2) > h->smem_optin)
         return fail(ST_ERR_UNSUPPORTED, "st_fdm_setup: a front of the sparse-direct solver exceeds shared memory");
     std::vector<MfFrontDev> fd(P.fronts.size());
     for (size_t i = 0; i < P.fronts.size(); ++i) {

@@ -205,7 +205,8 @@ __global__ void __launch_bounds__(MF_THREADS) k_mf_factor(MfArgs<T> a) {
 template <typename T>
 __global__ void __launch_bounds__(MF_THREADS) k_mf_fwd(MfArgs<T> a) {
     extern __shared__ __align__(16) unsigned char mf_smem[];
-    C<T>* x = reinterpret_cast<C<T>*>(mf_smem);   // [f]
+    C<T>* tri = reinterpret_cast<C<T>*>(mf_smem);  // [32][33] the block's triangle of L, staged
+    C<T>* x = tri + 32 * 33;                        // [f]
     const MfFrontDev fr = a.fronts[a.level_fronts[a.lvl_off + blockIdx.x]];
     const int k = a.k0 + blockIdx.y;
     const int tid = threadIdx.x, nth = blockDim.x, lane = tid & 31, warp = tid >> 5;
@@ -228,11 +229,17 @@ __global__ void __launch_bounds__(MF_THREADS) k_mf_fwd(MfArgs<T> a) {
     }
     for (int q0 = 0; q0 < np; q0 += 32) {
         const int wq = min(32, np - q0);
+        // stage the block's triangle (coalesced: consecutive threads, consecutive rows of a column)
+        for (int i = tid; i < wq * 32; i += nth) {
+            const int c = i >> 5, r = i & 31;
+            if (r < wq) tri[r * 33 + c] = Fp[(size_t)(q0 + c) * f + q0 + r];
+        }
+        __syncthreads();
         if (warp == 0) {
             C<T> v = lane < wq ? x[q0 + lane] : mk<T>(0, 0);
             for (int q = 0; q < wq; ++q) {
                 const C<T> z = shfl_c<T>(v, q);
-                if (lane > q && lane < wq) cfms<T>(v, Fp[(size_t)(q0 + q) * f + q0 + lane], z);
+                if (lane > q && lane < wq) cfms<T>(v, tri[lane * 33 + q], z);
             }
             if (lane < wq) x[q0 + lane] = v;
         }
@@ -252,7 +259,8 @@ __global__ void __launch_bounds__(MF_THREADS) k_mf_fwd(MfArgs<T> a) {
 template <typename T>
 __global__ void __launch_bounds__(MF_THREADS) k_mf_bwd(MfArgs<T> a) {
     extern __shared__ __align__(16) unsigned char mf_smem[];
-    C<T>* x = reinterpret_cast<C<T>*>(mf_smem);   // [f]
+    C<T>* tri = reinterpret_cast<C<T>*>(mf_smem);  // [32][33] the block's triangle of L, staged
+    C<T>* x = tri + 32 * 33;                        // [f]
     const MfFrontDev fr = a.fronts[a.level_fronts[a.lvl_off + blockIdx.x]];
     const int k = a.k0 + blockIdx.y;
     const int tid = threadIdx.x, nth = blockDim.x, lane = tid & 31, warp = tid >> 5, nwarps = nth >> 5;
@@ -276,12 +284,16 @@ __global__ void __launch_bounds__(MF_THREADS) k_mf_bwd(MfArgs<T> a) {
             }
             if (lane == 0) x[q0 + q] = csub<T>(x[q0 + q], acc);
         }
+        for (int i = tid; i < wq * 32; i += nth) {
+            const int c = i >> 5, r = i & 31;
+            if (r < wq) tri[r * 33 + c] = Fp[(size_t)(q0 + c) * f + q0 + r];
+        }
         __syncthreads();
         if (warp == 0) {
             C<T> v = lane < wq ? x[q0 + lane] : mk<T>(0, 0);
             for (int i = wq - 1; i >= 0; --i) {
                 const C<T> wi = shfl_c<T>(v, i);
-                if (lane < i) cfms<T>(v, Fp[(size_t)(q0 + lane) * f + q0 + i], wi);
+                if (lane < i) cfms<T>(v, tri[i * 33 + lane], wi);
             }
             if (lane < wq) x[q0 + lane] = v;
         }
@@ -313,7 +325,7 @@ template <typename T>
 cudaError_t mf_solve_launch(MfArgs<T> a, int lvl_off, int nfronts, int nsys, int max_front, bool fwd, cudaStream_t st) {
     if (nfronts <= 0 || nsys <= 0) return cudaSuccess;
     a.lvl_off = lvl_off;
-    const size_t smem = sizeof(C<T>) * (size_t)max_front;
+    const size_t smem = sizeof(C<T>) * ((size_t)max_front + 32 * 33);
     cudaError_t e;
     if (fwd) {
         e = cudaFuncSetAttribute(k_mf_fwd<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
