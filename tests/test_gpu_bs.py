@@ -3,7 +3,7 @@ oracle: the explicit space-time system solved by SuperLU, and the oracle's own B
 
 Bar: FP64 <= 1e-11 relative l2.  Where kappa_2(X_t) is large (P2 on a graded temporal mesh), the
 FDM's FP64 result carries that conditioning's rounding while Bartels-Stewart, whose Z is unitary,
-does not: both errors are printed and Bartels-Stewart's is asserted at the tighter level."""
+does not: both errors are printed, and Bartels-Stewart's is asserted to be no larger."""
 import numpy as np
 import pytest
 
