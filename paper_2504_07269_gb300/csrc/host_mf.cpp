@@ -19,7 +19,7 @@
 // independent.
 #include <algorithm>
 #include <cmath>
-#include <functional>
+#include <map>
 #include <numeric>
 #include <vector>
 
@@ -220,6 +220,73 @@ st_status build_mf_plan(const MeshSpace& ms, int leaf, MfPlan& P) {
     P.level_fronts.assign(F, 0);
     std::vector<int> fill(P.level_ptr.begin(), P.level_ptr.end() - 1);
     for (int f = 0; f < F; ++f) P.level_fronts[fill[P.fronts[f].height]++] = f;
+    // Update matrices live from their front's level until their parent's level has assembled them.
+    // Their offsets come from a first-fit allocation replayed level by level (a level's new matrices
+    // are placed before its children's are released), so the storage is the peak of the live set,
+    // not the sum over all fronts.
+    {
+        std::map<long long, long long> free_blocks;   // offset -> size
+        long long top = 0;
+        auto alloc = [&](long long sz) -> long long {
+            for (auto it = free_blocks.begin(); it != free_blocks.end(); ++it)
+                if (it->second >= sz) {
+                    const long long off = it->first, rest = it->second - sz;
+                    free_blocks.erase(it);
+                    if (rest > 0) free_blocks[off + sz] = rest;
+                    return off;
+                }
+            const long long off = top;
+            top += sz;
+            return off;
+        };
+        auto release = [&](long long off, long long sz) {
+            auto it = free_blocks.emplace(off, sz).first;
+            auto nx = std::next(it);
+            if (nx != free_blocks.end() && it->first + it->second == nx->first) {
+                it->second += nx->second;
+                free_blocks.erase(nx);
+            }
+            if (it != free_blocks.begin()) {
+                auto pv = std::prev(it);
+                if (pv->first + pv->second == it->first) {
+                    pv->second += it->second;
+                    free_blocks.erase(it);
+                }
+            }
+        };
+        for (int h = 0; h <= maxh; ++h) {
+            for (int i = P.level_ptr[h]; i < P.level_ptr[h + 1]; ++i) {
+                MfFront& fr = P.fronts[P.level_fronts[i]];
+                const long long sz = (long long)fr.nu * fr.nu;
+                fr.uoff = sz > 0 ? alloc(sz) : 0;
+            }
+            for (int i = P.level_ptr[h]; i < P.level_ptr[h + 1]; ++i) {
+                const MfFront& fr = P.fronts[P.level_fronts[i]];
+                for (int c = 0; c < fr.child_cnt; ++c) {
+                    const MfFront& ch = P.fronts[P.children[fr.child_off + c]];
+                    if (ch.nu > 0) release(ch.uoff, (long long)ch.nu * ch.nu);
+                }
+            }
+        }
+        P.update_entries = top;
+        // check: at every level, the update matrices alive then (produced at or below it, consumed at
+        // or above it) occupy disjoint ranges
+        for (int h = 0; h <= maxh; ++h) {
+            std::vector<std::pair<long long, long long>> live;
+            for (const MfFront& fr : P.fronts) {
+                if (fr.nu == 0 || fr.height > h) continue;
+                const int consumed = fr.parent >= 0 ? P.fronts[fr.parent].height : maxh + 1;
+                if (consumed < h) continue;
+                live.push_back({fr.uoff, fr.uoff + (long long)fr.nu * fr.nu});
+            }
+            std::sort(live.begin(), live.end());
+            for (size_t i = 1; i < live.size(); ++i)
+                if (live[i].first < live[i - 1].second)
+                    return fail(ST_ERR_ARG, "multifrontal plan: overlapping update matrices");
+            for (const auto& iv : live)
+                if (iv.second > top) return fail(ST_ERR_ARG, "multifrontal plan: update matrix beyond the storage");
+        }
+    }
     return ST_OK;
 }
 

@@ -48,7 +48,7 @@ __device__ __forceinline__ bool mf_bad(C<T> d) {
 
 // ------------------------------------------------------------------ factorisation
 template <typename T>
-__global__ void __launch_bounds__(MF_THREADS) k_mf_factor(MfArgs<T> a) {
+__global__ void __launch_bounds__(MF_THREADS, 2) k_mf_factor(MfArgs<T> a) {
     constexpr int NB = MfNB<T>::v;
     extern __shared__ __align__(16) unsigned char mf_smem[];
     C<T>* Tt = reinterpret_cast<C<T>*>(mf_smem);            // [NB][NB + 1] top block, row-major
@@ -315,6 +315,9 @@ cudaError_t mf_factor_launch(MfArgs<T> a, int lvl_off, int nfronts, int nsys, cu
     a.lvl_off = lvl_off;
     const size_t smem = mf_factor_smem<T>();
     cudaError_t e = cudaFuncSetAttribute(k_mf_factor<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_mf_factor<T>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                 cudaSharedmemCarveoutMaxShared);
     if (e != cudaSuccess) return e;
     k_mf_factor<T><<<dim3(nfronts, nsys), MF_THREADS, smem, st>>>(a);
     note_launches(1);
