@@ -446,7 +446,7 @@ def run_ours(args):
     if args.spatial == "multifrontal":
         # the plan's factorisation flops (8 per complex multiply-add over every front's eliminations)
         # plus both substitutions over the stored factor blocks, per system
-        plan = stfdm.st_space_mf_plan(h.space, 64)
+        plan = stfdm.st_space_mf_plan(h.space, 0)
         flops = pr.n_t * (plan["flops"] + 2.0 * 8.0 * plan["factor_entries"])
     else:
         # complex MAC = 8 real flops; per system n_x b^2/2 for the factorisation and n_x b for each of

@@ -178,7 +178,7 @@ st_status st_assemble_mesh(int dim, int p_x, int n_vertices, const double* coord
 st_status st_space_get_mesh(const st_space* s, int* dim, int* p_x, int* n_x, long long* nnz, int* rowptr, int* col,
                             double* M, double* A, double* xyz);
 /* The sparse-direct solver's plan for a space (host only): nested dissection by coordinate bisection
- * with leaves of at most `leaf` DOFs (<= 0: 64) and its multifrontal assembly tree.  Outputs (any may
+ * with leaves of at most `leaf` DOFs (<= 0: 16, the solver's own choice) and its multifrontal assembly tree.  Outputs (any may
  * be NULL): fronts, launch levels, the largest front, factor entries per system, real flops of one
  * factorisation (8 per complex multiply-add), perm[n_x] (elimination position -> DOF), per front
  * its first pivot position, pivot count and update-row count, and the update rows of all fronts

@@ -399,28 +399,15 @@ template <typename T>
 cudaError_t mf_levels(const st_fdm* h, MfArgs<T>& a, int k0, int cnt, int what, cudaStream_t st) {
     const MfPlan& P = h->mf;
     const int H = (int)P.level_ptr.size() - 1;
-    {
-        a.k0 = k0;
-        if (what == 0) {
-            for (int l = 0; l < H; ++l) {
-                cudaError_t e = mf_factor_launch<T>(a, P.level_ptr[l], P.level_ptr[l + 1] - P.level_ptr[l], cnt, st);
-                if (e != cudaSuccess) return e;
-            }
-        } else if (what == 1) {
-            for (int l = 0; l < H; ++l) {
-                cudaError_t e = mf_solve_launch<T>(a, P.level_ptr[l], P.level_ptr[l + 1] - P.level_ptr[l], cnt,
-                                                   P.max_front, true, st);
-                if (e != cudaSuccess) return e;
-            }
-        } else {
-            for (int l = H - 1; l >= 0; --l) {
-                cudaError_t e = mf_solve_launch<T>(a, P.level_ptr[l], P.level_ptr[l + 1] - P.level_ptr[l], cnt,
-                                                   P.max_front, false, st);
-                if (e != cudaSuccess) return e;
-            }
-        }
-        return cudaSuccess;
+    a.k0 = k0;
+    for (int i = 0; i < H; ++i) {
+        const int l = (what == 2) ? H - 1 - i : i;   // backward substitution from the root
+        const int n = P.level_ptr[l + 1] - P.level_ptr[l];
+        const int n32 = P.level_n32[l], n64 = P.level_n64[l];
+        cudaError_t e = mf_level_launch<T>(a, P.level_ptr[l], n32, n64, n - n32 - n64, cnt, P.max_front, what, st);
+        if (e != cudaSuccess) return e;
     }
+    return cudaSuccess;
 }
 
 // the launch arguments common to every banded kernel of a handle (windows and factor storage unset)
@@ -1176,7 +1163,7 @@ st_status setup_spatial(st_fdm* h, int choice) {
         if (s != ST_OK) return s;
     }
     try {
-        s = build_mf_plan(*ms, 64, h->mf);
+        s = build_mf_plan(*ms, MF_DEFAULT_LEAF, h->mf);
     } catch (const std::bad_alloc&) {
         return fail(ST_ERR_OOM, "st_fdm_setup: multifrontal plan (host)");
     }

@@ -80,13 +80,16 @@ struct MfPlan {
     std::vector<MfFront> fronts;
     std::vector<int> urows, relpos, children;
     std::vector<int> orig_r, orig_c, orig_k;
-    std::vector<int> level_ptr, level_fronts;   // fronts by height (leaves first)
+    std::vector<int> level_ptr, level_fronts;   // fronts by height (leaves first); within a level the
+                                                // fronts with f <= 32, then f <= 64, then the rest
+    std::vector<int> level_n32, level_n64;      // per level: fronts with f <= 32, with 32 < f <= 64
     long long factor_entries = 0, update_entries = 0, uvec_entries = 0;
     int max_front = 0, max_np = 0;
     double flops_cmac = 0;             // complex multiply-adds of one factorisation
 };
 
 st_status build_mf_plan(const MeshSpace& ms, int leaf, MfPlan& out);
+constexpr int MF_DEFAULT_LEAF = 16;
 
 // host FP64 dense linear algebra (column-major n x n unless stated)
 namespace la {

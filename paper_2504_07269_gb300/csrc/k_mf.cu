@@ -302,6 +302,234 @@ __global__ void __launch_bounds__(MF_THREADS) k_mf_bwd(MfArgs<T> a) {
     for (int t = tid; t < np; t += nth) g[a.perm[fr.first + t]] = x[t];
 }
 
+// ------------------------------------------------------------------ small fronts
+// Fronts with f <= FM (32 or 64): one warp per (front, system), W warps per CTA, the whole front's
+// lower triangle packed by rows in the warp's shared-memory tile (entry (r, c), c <= r, at
+// r (r + 1) / 2 + c); lane l owns rows l, l + 32, ...  Items are (front, system) pairs, system
+// fastest, so the warps of a CTA share a front's metadata.
+template <typename T, int FM>
+struct SmallCfg {
+    static constexpr int R = FM / 32;                                                      // rows per lane
+    static constexpr int W = (FM == 32) ? 8 : (sizeof(T) == 4 ? 6 : 3);                    // warps per CTA
+    static constexpr int TILE = FM * (FM + 1) / 2 + FM;                                    // entries per warp
+    static constexpr size_t SMEM = sizeof(C<T>) * (size_t)W * TILE;
+};
+__device__ __forceinline__ int tri_row(int r) { return (r * (r + 1)) >> 1; }
+
+template <typename T, int FM>
+__global__ void __launch_bounds__(SmallCfg<T, FM>::W * 32) k_mf_factor_small(MfArgs<T> a, int nfronts, int nsys) {
+    using Cfg = SmallCfg<T, FM>;
+    constexpr int R = Cfg::R;
+    extern __shared__ __align__(16) unsigned char mf_smem[];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const long long item = (long long)blockIdx.x * Cfg::W + warp;
+    if (item >= (long long)nfronts * nsys) return;
+    const int fi = (int)(item / nsys), ks = (int)(item - (long long)fi * nsys);
+    C<T>* F = reinterpret_cast<C<T>*>(mf_smem) + (size_t)warp * Cfg::TILE;
+    const MfFrontDev fr = a.fronts[a.level_fronts[a.lvl_off + fi]];
+    const int k = a.k0 + ks;
+    const int np = fr.np, nu = fr.nu, f = np + nu;
+    const C<T> s = a.shifts[k];
+    C<T>* Fp = a.fac + (size_t)(a.fac_keep ? k : ks) * a.fac_stride + fr.foff;
+    C<T>* S = a.upd + (size_t)ks * a.upd_stride + fr.uoff;
+#pragma unroll
+    for (int i = 0; i < R; ++i) {
+        const int r = lane + 32 * i;
+        if (r < f)
+            for (int c = 0; c <= r; ++c) F[tri_row(r) + c] = mk<T>(0, 0);
+    }
+    __syncwarp();
+    for (int e = lane; e < fr.orig_cnt; e += 32) {
+        const int q = a.orig_k[fr.orig_off + e];
+        const double m = a.Mv[q], av = a.Av[q];
+        F[tri_row(a.orig_r[fr.orig_off + e]) + a.orig_c[fr.orig_off + e]] =
+            mk<T>((T)(m + (double)s.x * av), (T)((double)s.y * av));
+    }
+    __syncwarp();
+    for (int ci = 0; ci < fr.child_cnt; ++ci) {
+        const MfFrontDev ch = a.fronts[a.children[fr.child_off + ci]];
+        const C<T>* Sc = a.upd + (size_t)ks * a.upd_stride + ch.uoff;
+        const int* rp = a.relpos + ch.relpos_off;
+        const int cn = ch.nu;
+        for (int i = lane; i < cn * cn; i += 32) {
+            const int t2 = i / cn, t1 = i - t2 * cn;
+            if (t1 < t2) continue;
+            C<T>& dst = F[tri_row(rp[t1]) + rp[t2]];
+            const C<T> v = Sc[i];
+            dst.x += v.x;
+            dst.y += v.y;
+        }
+        __syncwarp();
+    }
+    // right-looking unscaled elimination of the np pivots; the trailing block is the update matrix
+    bool bad = false;
+    for (int q = 0; q < np; ++q) {
+        C<T> d = F[tri_row(q) + q];
+        if (mf_bad<T>(d)) {
+            bad = true;
+            d = mk<T>((T)1e-30, 0);
+        }
+        const C<T> di = cinv<T>(d);
+        C<T> u[R];
+#pragma unroll
+        for (int i = 0; i < R; ++i) {
+            const int r = lane + 32 * i;
+            u[i] = (r > q && r < f) ? cmul<T>(F[tri_row(r) + q], di) : mk<T>(0, 0);   // L(r, q)
+        }
+        for (int c = q + 1; c < f; ++c) {
+            const C<T> uc = F[tri_row(c) + q];              // d_q L(c, q), still unscaled
+#pragma unroll
+            for (int i = 0; i < R; ++i) {
+                const int r = lane + 32 * i;
+                if (r >= c && r < f) cfms<T>(F[tri_row(r) + c], u[i], uc);
+            }
+        }
+        __syncwarp();
+#pragma unroll
+        for (int i = 0; i < R; ++i) {
+            const int r = lane + 32 * i;
+            if (r > q && r < f) F[tri_row(r) + q] = u[i];
+        }
+        if (lane == 0) F[tri_row(q) + q] = d;
+        __syncwarp();
+    }
+    if (bad && lane == 0) atomicExch(a.status, 1);
+    // factor block (f x np, column-major) and update matrix (nu x nu, column-major) out
+    for (int c = 0; c < np; ++c)
+#pragma unroll
+        for (int i = 0; i < R; ++i) {
+            const int r = lane + 32 * i;
+            if (r >= c && r < f) Fp[(size_t)c * f + r] = F[tri_row(r) + c];
+        }
+    for (int c = np; c < f; ++c)
+#pragma unroll
+        for (int i = 0; i < R; ++i) {
+            const int r = lane + 32 * i;
+            if (r >= c && r < f) S[(size_t)(c - np) * nu + (r - np)] = F[tri_row(r) + c];
+        }
+}
+
+template <typename T, int FM>
+__global__ void __launch_bounds__(SmallCfg<T, FM>::W * 32)
+k_mf_solve_small(MfArgs<T> a, int nfronts, int nsys, int fwd) {
+    using Cfg = SmallCfg<T, FM>;
+    constexpr int R = Cfg::R;
+    extern __shared__ __align__(16) unsigned char mf_smem[];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const long long item = (long long)blockIdx.x * Cfg::W + warp;
+    if (item >= (long long)nfronts * nsys) return;
+    const int fi = (int)(item / nsys), ks = (int)(item - (long long)fi * nsys);
+    C<T>* L = reinterpret_cast<C<T>*>(mf_smem) + (size_t)warp * Cfg::TILE;  // the factor block, packed rows
+    C<T>* x = L + FM * (FM + 1) / 2;                                           // [FM]
+    const MfFrontDev fr = a.fronts[a.level_fronts[a.lvl_off + fi]];
+    const int k = a.k0 + ks;
+    const int np = fr.np, nu = fr.nu, f = np + nu;
+    const C<T>* Fp = a.fac + (size_t)(a.fac_keep ? k : ks) * a.fac_stride + fr.foff;
+    C<T>* g = a.rhs + (size_t)k * a.n;
+    for (int c = 0; c < np; ++c)
+#pragma unroll
+        for (int i = 0; i < R; ++i) {
+            const int r = lane + 32 * i;
+            if (r >= c && r < f) L[tri_row(r) + c] = Fp[(size_t)c * f + r];
+        }
+    if (fwd) {
+        C<T>* uv = a.uvec + (size_t)ks * a.uvec_stride;
+#pragma unroll
+        for (int i = 0; i < R; ++i) {
+            const int r = lane + 32 * i;
+            if (r < f) x[r] = r < np ? g[a.perm[fr.first + r]] : mk<T>(0, 0);
+        }
+        __syncwarp();
+        for (int ci = 0; ci < fr.child_cnt; ++ci) {
+            const MfFrontDev ch = a.fronts[a.children[fr.child_off + ci]];
+            const int* rp = a.relpos + ch.relpos_off;
+            for (int t = lane; t < ch.nu; t += 32) {
+                const C<T> v = uv[ch.uvoff + t];
+                C<T>& d = x[rp[t]];
+                d.x += v.x;
+                d.y += v.y;
+            }
+            __syncwarp();
+        }
+        for (int q = 0; q < np; ++q) {
+            const C<T> z = x[q];
+#pragma unroll
+            for (int i = 0; i < R; ++i) {
+                const int r = lane + 32 * i;
+                if (r > q && r < f) cfms<T>(x[r], L[tri_row(r) + q], z);
+            }
+            __syncwarp();
+        }
+#pragma unroll
+        for (int i = 0; i < R; ++i) {
+            const int r = lane + 32 * i;
+            if (r < np) g[a.perm[fr.first + r]] = cmul<T>(x[r], cinv<T>(L[tri_row(r) + r]));
+            else if (r < f) uv[fr.uvoff + r - np] = x[r];
+        }
+    } else {
+#pragma unroll
+        for (int i = 0; i < R; ++i) {
+            const int r = lane + 32 * i;
+            if (r < f) x[r] = g[a.perm[r < np ? fr.first + r : a.urows[fr.urows_off + r - np]]];
+        }
+        __syncwarp();
+        for (int q = np - 1; q >= 0; --q) {
+            C<T> acc = mk<T>(0, 0);
+#pragma unroll
+            for (int i = 0; i < R; ++i) {
+                const int r = lane + 32 * i;
+                if (r > q && r < f) cfma<T>(acc, L[tri_row(r) + q], x[r]);
+            }
+#pragma unroll
+            for (int off = 16; off > 0; off >>= 1) {
+                acc.x += __shfl_xor_sync(0xffffffffu, acc.x, off);
+                acc.y += __shfl_xor_sync(0xffffffffu, acc.y, off);
+            }
+            if (lane == 0) x[q] = csub<T>(x[q], acc);
+            __syncwarp();
+        }
+#pragma unroll
+        for (int i = 0; i < R; ++i) {
+            const int r = lane + 32 * i;
+            if (r < np) g[a.perm[fr.first + r]] = x[r];
+        }
+    }
+}
+
+template <typename T, int FM>
+cudaError_t mf_small_launch(MfArgs<T> a, int lvl_off, int nfronts, int nsys, int what, cudaStream_t st) {
+    using Cfg = SmallCfg<T, FM>;
+    if (nfronts <= 0 || nsys <= 0) return cudaSuccess;
+    a.lvl_off = lvl_off;
+    const long long items = (long long)nfronts * nsys;
+    const long long blocks = (items + Cfg::W - 1) / Cfg::W;
+    if (blocks > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
+    cudaError_t e;
+    if (what == 0) {
+        e = cudaFuncSetAttribute(k_mf_factor_small<T, FM>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Cfg::SMEM);
+        if (e != cudaSuccess) return e;
+        k_mf_factor_small<T, FM><<<(unsigned)blocks, Cfg::W * 32, Cfg::SMEM, st>>>(a, nfronts, nsys);
+    } else {
+        e = cudaFuncSetAttribute(k_mf_solve_small<T, FM>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Cfg::SMEM);
+        if (e != cudaSuccess) return e;
+        k_mf_solve_small<T, FM><<<(unsigned)blocks, Cfg::W * 32, Cfg::SMEM, st>>>(a, nfronts, nsys, what == 1 ? 1 : 0);
+    }
+    note_launches(1);
+    return cudaGetLastError();
+}
+
+// one launch level: fronts [lvl_off, lvl_off + n32) have f <= 32, the next n64 have f <= 64, the rest
+// are large; what: 0 factorise, 1 forward, 2 backward
+template <typename T>
+cudaError_t mf_level_launch(MfArgs<T> a, int lvl_off, int n32, int n64, int nlarge, int nsys, int max_front, int what,
+                            cudaStream_t st) {
+    cudaError_t e = mf_small_launch<T, 32>(a, lvl_off, n32, nsys, what, st);
+    if (e == cudaSuccess) e = mf_small_launch<T, 64>(a, lvl_off + n32, n64, nsys, what, st);
+    if (e != cudaSuccess || nlarge <= 0) return e;
+    if (what == 0) return mf_factor_launch<T>(a, lvl_off + n32 + n64, nlarge, nsys, st);
+    return mf_solve_launch<T>(a, lvl_off + n32 + n64, nlarge, nsys, max_front, what == 1, st);
+}
+
 // ------------------------------------------------------------------ launchers
 template <typename T>
 size_t mf_factor_smem() {
@@ -343,6 +571,8 @@ cudaError_t mf_solve_launch(MfArgs<T> a, int lvl_off, int nfronts, int nsys, int
     return cudaGetLastError();
 }
 
+template cudaError_t mf_level_launch<float>(MfArgs<float>, int, int, int, int, int, int, int, cudaStream_t);
+template cudaError_t mf_level_launch<double>(MfArgs<double>, int, int, int, int, int, int, int, cudaStream_t);
 template cudaError_t mf_factor_launch<float>(MfArgs<float>, int, int, int, cudaStream_t);
 template cudaError_t mf_factor_launch<double>(MfArgs<double>, int, int, int, cudaStream_t);
 template cudaError_t mf_solve_launch<float>(MfArgs<float>, int, int, int, int, bool, cudaStream_t);

@@ -35,7 +35,8 @@ def rel(a, b):
     return float(np.linalg.norm(a - b) / np.linalg.norm(b))
 
 
-def test_c2_check_size_vs_space_eig_oracle(dev):
+@pytest.mark.parametrize("solver", ["banded", "multifrontal"])
+def test_c2_check_size_vs_space_eig_oracle(dev, solver):
     from paper_2504_07269_gb300 import stfdm
 
     pr = synth.config_problem("c2check")
@@ -48,12 +49,12 @@ def test_c2_check_size_vs_space_eig_oracle(dev):
     psi0 = synth.psi0_c1(x1, x2)
     ref = solve.solve_space_eig(M_t, B_t, M_x, A_x, F - np.outer(m_t, A_x @ psi0)) + psi0[None, :]
     _, r_ref = solve.residual(M_t, B_t, M_x, A_x, ref - psi0[None, :], F - np.outer(m_t, A_x @ psi0))
-    h = stfdm.setup_problem(pr.n, pr.p_t, pr.t_nodes, device=0)
+    h = stfdm.setup_problem(pr.n, pr.p_t, pr.t_nodes, device=0, spatial_solver=solver)
     Fd, p0 = torch.from_numpy(F).to(dev), torch.from_numpy(psi0).to(dev)
     psi64, _ = stfdm.st_fdm_solve(h, Fd, p0, precision="fp64")
     psim, info = stfdm.st_fdm_solve(h, Fd, p0, precision="mixed")
     e64, em = rel(psi64.cpu().numpy(), ref), rel(psim.cpu().numpy(), ref)
-    print(f"64x64/128 ({pr.unknowns} unknowns): oracle residual {r_ref:.1e}; fp64 {e64:.2e}, mixed {em:.2e} "
+    print(f"64x64/128 {solver} ({pr.unknowns} unknowns): oracle residual {r_ref:.1e}; fp64 {e64:.2e}, mixed {em:.2e} "
           f"({info['sweeps']} FP32 applications, residual {info['rel_residual']:.1e})")
     assert e64 <= 1e-11
     assert em <= 1e-9
@@ -61,8 +62,8 @@ def test_c2_check_size_vs_space_eig_oracle(dev):
     assert np.abs(psim.cpu().numpy() - exact).max() < 2e-3     # discretisation error at this mesh
 
 
-@pytest.mark.parametrize("n,p,N", [(260, 2, 4), (384, 1, 4)])
-def test_wide_band_vs_refined_cpu_fdm(dev, n, p, N):
+@pytest.mark.parametrize("n,p,N,solver", [(260, 2, 4, "banded"), (384, 1, 4, "banded"), (384, 1, 4, "multifrontal")])
+def test_wide_band_vs_refined_cpu_fdm(dev, n, p, N, solver):
     from paper_2504_07269_gb300 import stfdm
 
     t = synth.uniform_time_nodes(N, 1.0)
@@ -74,7 +75,7 @@ def test_wide_band_vs_refined_cpu_fdm(dev, n, p, N):
     F = solve.kron_apply(M_t, B_t, M_x, A_x, u) + np.outer(m_t, A_x @ psi0)   # psi = u + psi0
     rep = {}
     ref = cpu_fdm.cpu_fdm_refined(n, p, t, F, psi0, sweeps=1, report=rep)
-    h = stfdm.setup_problem(n, p, t, device=0)
+    h = stfdm.setup_problem(n, p, t, device=0, spatial_solver=solver)
     assert h.m + 1 == n and h.m + 1 > 256
     Fd, p0 = torch.from_numpy(F).to(dev), torch.from_numpy(psi0).to(dev)
     psi64, _ = stfdm.st_fdm_solve(h, Fd, p0, precision="fp64")
@@ -84,7 +85,7 @@ def test_wide_band_vs_refined_cpu_fdm(dev, n, p, N):
     psim, info = stfdm.st_fdm_solve(h, Fd, p0, precision="mixed", tol=1e-13, max_sweeps=60)
     e64, em = rel(psi64.cpu().numpy(), ref), rel(psim.cpu().numpy(), ref)
     exact = u + psi0[None, :]
-    print(f"b={n} P{p} n_t={p * N} ({u.size} unknowns): oracle residuals {rep['residuals']}, oracle vs u* "
+    print(f"b={n} P{p} n_t={p * N} {solver} ({u.size} unknowns): oracle residuals {rep['residuals']}, oracle vs u* "
           f"{rel(ref, exact):.1e}; fp64 {e64:.2e}, mixed {em:.2e} ({info['sweeps']} FP32 applications); "
           f"fp64 vs u* {rel(psi64.cpu().numpy(), exact):.1e}")
     assert rep["residuals"][-1] <= 1e-14

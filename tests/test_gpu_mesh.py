@@ -33,6 +33,8 @@ def rel(a, b):
 MESHES = {
     "tri": lambda: synth.square_delaunay_mesh(14, jitter=0.3, seed=31),
     "tet": lambda: synth.cube_tet_mesh(6, jitter=0.2, seed=32),
+    "tet8": lambda: synth.cube_tet_mesh(8, jitter=0.2, seed=34),
+    "tri40": lambda: synth.square_delaunay_mesh(40, jitter=0.3, seed=35),
 }
 
 CASES = [
@@ -41,6 +43,8 @@ CASES = [
     ("tri", 2, 2, 5, 0.8),
     ("tet", 1, 1, 7, 1.0),
     ("tet", 2, 1, 4, 0.5),
+    ("tet8", 2, 1, 3, 0.5),      # fronts of every size class (one warp, up to 64, larger)
+    ("tri40", 2, 1, 5, 1.0),
 ]
 
 
