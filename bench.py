@@ -56,8 +56,10 @@ def parse_args(argv=None):
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--config", default="c3")
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64", "fp32"])
-    ap.add_argument("--spatial", default="banded", choices=["banded", "multifrontal"],
-                    help="spatial solver of step 3: banded LDL^T (default) or the sparse-direct multifrontal one")
+    ap.add_argument("--spatial", default="multifrontal", choices=["banded", "multifrontal"],
+                    help="spatial solver of step 3: the sparse-direct multifrontal LDL^T (default) or banded LDL^T")
+    ap.add_argument("--no-compare-banded", dest="compare_banded", action="store_false",
+                    help="skip the banded solver's comparison measurement")
     ap.add_argument("--no-fp64-check", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--profile-step", action="store_true",
@@ -156,9 +158,10 @@ def measured_peaks():
 
 
 def kernel_source_sha():
-    """Hash of the source of the kernels the FP32 spatial solve runs (the blocked-panel factor
-    kernel's section of k_band.cu, the substitution kernels and the shared device header): the
-    recorded DRAM traffic is used only while this is unchanged."""
+    """Hash of the source of the kernels the FP32 banded spatial solve runs (the blocked-panel factor
+    kernel's section of k_band.cu, the substitution kernels, the asynchronous-copy helpers, and the
+    complex helpers and launch arguments of the device header): the recorded DRAM traffic is used
+    only while this is unchanged."""
     csrc = os.path.join(ROOT, "paper_2504_07269_gb300", "csrc")
     with open(os.path.join(csrc, "k_band.cu")) as fh:
         text = fh.read()
@@ -168,10 +171,11 @@ def kernel_source_sha():
     for name in ("k_subst.cu", "async.cuh", "device.cuh"):
         with open(os.path.join(csrc, name)) as fh:
             part = fh.read()
-        if name == "device.cuh":   # the handle struct is host-side bookkeeping, not kernel code
-            a = part.find("struct st_fdm {")
-            if a >= 0:
-                part = part[:a] + part[part.index("\n};", a) + 3:]
+        if name == "device.cuh":   # only what the banded kernels consume: the complex helpers, BandArgs
+            a = part.index("// ------------------------------------------------------------------ complex helpers")
+            b = part.index("// ------------------------------------------------------------------ handle")
+            c = part.index("struct BandArgs {")
+            part = part[a:b] + part[c:part.index("\n};", c) + 3]
         h.update(part.encode())
     return h.hexdigest()[:16]
 
@@ -313,6 +317,7 @@ def run_ours(args):
     t0 = time.perf_counter()
     h = stfdm.setup_problem(pr.n, pr.p_t, pr.t_nodes, Lx=pr.Lx, Ly=pr.Ly, device=local, spatial_solver=args.spatial)
     setup_s = time.perf_counter() - t0
+    kappa = h.kappa
     F, p0 = make_inputs(pr, h, dev)
     dt = torch.complex64 if args.precision == "fp32" else torch.complex128
     F = F.to(dt)
@@ -427,48 +432,20 @@ def run_ours(args):
         del ref, mine, F64, p064
         torch.cuda.empty_cache()
 
-    # ---- roofline of the dominant kernel: the banded LDL^T factor-and-solve (FP32 / FP64)
+    # ---- rooflines: the multifrontal substitution pass (the kernels of every later FP32 application,
+    # HBM) and its factorisation (ALU), or the banded factor-and-solve (ALU)
     kprec = "fp64" if args.precision == "fp64" else "fp32"
-    kdt = torch.complex128 if kprec == "fp64" else torch.complex64
-    G0 = torch.from_numpy(synth.cn01((pr.n_t, pr.n_x), seed=11)).to(dev).to(kdt)
-    Gw = torch.empty_like(G0)
-    times = []
-    for r in range(3):
-        Gw.copy_(G0)
-        torch.cuda.synchronize()
-        e0.record()
-        stfdm.st_spatial_solve(h, kprec, Gw, Gw)
-        e1.record()
-        torch.cuda.synchronize()
-        times.append(e0.elapsed_time(e1) * 1e-3)
-    tk = statistics.median(times)
-    b = pr.n - 1 + 1
     if args.spatial == "multifrontal":
-        # the plan's factorisation flops (8 per complex multiply-add over every front's eliminations)
-        # plus both substitutions over the stored factor blocks, per system
-        plan = stfdm.st_space_mf_plan(h.space, 0)
-        flops = pr.n_t * (plan["flops"] + 2.0 * 8.0 * plan["factor_entries"])
+        roof, roof_factor = multifrontal_rooflines(stfdm, h, pr, kprec, dev, clocks)
     else:
-        # complex MAC = 8 real flops; per system n_x b^2/2 for the factorisation and n_x b for each of
-        # the two substitutions (the forward one fused into the factor kernel, the backward one a
-        # separate launch inside the timed region)
-        flops = 8.0 * pr.n_t * pr.n_x * (b * b / 2.0 + 2.0 * b)
-    props = torch.cuda.get_device_properties(dev)
-    max_mhz = (clocks or {}).get("sm_max_mhz") or (measured_peaks() or {}).get("sm_max_mhz", 2070.0)
-    lanes = 128 if kprec == "fp32" else 2             # FP32 / FP64 FMA lanes per SM per clock
-    peak = props.multi_processor_count * lanes * 2 * max_mhz * 1e6 / 1e12
-    achieved = flops / tk / 1e12
-    if args.spatial == "multifrontal":
-        kname = f"k_mf_factor<{'float' if kprec == 'fp32' else 'double'}> + k_mf_fwd + k_mf_bwd (all levels)"
-    elif kprec == "fp32":
-        kname = "k_band_factor_v4 (complex64, fused forward substitution) + k_subst_bwd<float>"
-    else:
-        kname = "k_band_factor_solve<double,32> + k_subst_bwd<double>"
-    roof = {"bound": "alu", "kernel": kname,
-            "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-            "traffic": profiled_traffic(args.config) if args.spatial == "banded" else None, "launch_ms": tk * 1e3,
-            "peak_basis": f"{props.multi_processor_count} SMs x {lanes} {kprec.upper()} FMA lanes x 2 x {max_mhz:.0f} MHz "
-                          "(derived, max SM clock)"}
+        roof, roof_factor = banded_roofline(stfdm, h, pr, kprec, dev, clocks, args.config), None
+
+    # ---- the banded solver (the fixed spatial design) on the same workload, for comparison
+    banded = None
+    if args.spatial == "multifrontal" and args.compare_banded and args.precision == "mixed":
+        del h
+        torch.cuda.empty_cache()
+        banded = banded_comparison(stfdm, pr, F, p0, psi, tol, etol, kprec, dev, clocks, args.config, local)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -491,19 +468,136 @@ def run_ours(args):
                 "restart": info.get("restart") if info else None,
                 "kept_systems": info.get("kept_systems") if info else None,
                 "final_rel_residual": info.get("rel_residual") if info else None,
-                "setup_s": setup_s, "kappa_x": h.kappa,
+                "setup_s": setup_s, "kappa_x": kappa,
                 "e2e": {"value": world * pr.unknowns / (e2e_ms * 1e-3), "unit": UNIT, "h2d_bytes_per_step": h2d,
                         "d2h_bytes_per_step": d2h, "h2d_ms": h2d_ms, "d2h_ms": d2h_ms,
                         "h2d_gbs": h2d / (h2d_ms * 1e6), "d2h_gbs": d2h / (d2h_ms * 1e6),
                         "timing": "same steps as value: events around H2D + solve + D2H (e2e) and the solve (value)"},
                 "gpu_launches": launches_per_step * args.steps,
-                "roofline": roof, "cpu_baseline": cpu, "clocks": clocks}
+                "roofline": roof, "roofline_factor": roof_factor, "banded": banded,
+                "cpu_baseline": cpu, "clocks": clocks}
         print(json.dumps(line))
     if world > 1:
         import torch.distributed as dist
 
         dist.destroy_process_group()
     return 0
+
+
+def _peak_alu(dev, clocks, kprec):
+    import torch
+
+    props = torch.cuda.get_device_properties(dev)
+    max_mhz = (clocks or {}).get("sm_max_mhz") or (measured_peaks() or {}).get("sm_max_mhz", 2070.0)
+    lanes = 128 if kprec == "fp32" else 2             # FP32 / FP64 FMA lanes per SM per clock
+    basis = (f"{props.multi_processor_count} SMs x {lanes} {kprec.upper()} FMA lanes x 2 x {max_mhz:.0f} MHz "
+             "(derived, max SM clock)")
+    return props.multi_processor_count * lanes * 2 * max_mhz * 1e6 / 1e12, basis
+
+
+def _time3(fn):
+    """Median of three CUDA-event timings of fn() on the current stream, seconds."""
+    import torch
+
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    times = []
+    for _ in range(3):
+        torch.cuda.synchronize()
+        e0.record()
+        fn()
+        e1.record()
+        torch.cuda.synchronize()
+        times.append(e0.elapsed_time(e1) * 1e-3)
+    return statistics.median(times)
+
+
+def banded_roofline(stfdm, h, pr, kprec, dev, clocks, config):
+    """The banded LDL^T factor-and-solve of all n_t systems (factor kernel with the fused forward
+    substitution, then the backward substitution), against the FP32 (or FP64) ALU peak."""
+    import torch
+
+    kdt = torch.complex128 if kprec == "fp64" else torch.complex64
+    G0 = torch.from_numpy(synth.cn01((pr.n_t, pr.n_x), seed=11)).to(dev).to(kdt)
+    Gw = torch.empty_like(G0)
+
+    def run():
+        Gw.copy_(G0)
+        stfdm.st_spatial_solve(h, kprec, Gw, Gw)
+
+    tk = _time3(run)            # the copy is 0.1% of the launch
+    b = pr.n
+    # complex MAC = 8 real flops; per system n_x b^2/2 for the factorisation and n_x b for each of the
+    # two substitutions (the forward one fused into the factor kernel)
+    flops = 8.0 * pr.n_t * pr.n_x * (b * b / 2.0 + 2.0 * b)
+    peak, basis = _peak_alu(dev, clocks, kprec)
+    achieved = flops / tk / 1e12
+    kname = ("k_band_factor_v4 (complex64, fused forward substitution) + k_subst_bwd<float>" if kprec == "fp32"
+             else "k_band_factor_solve<double,32> + k_subst_bwd<double>")
+    return {"bound": "alu", "kernel": kname, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+            "frac": achieved / peak, "traffic": profiled_traffic(config), "launch_ms": tk * 1e3,
+            "peak_basis": basis}
+
+
+def multifrontal_rooflines(stfdm, h, pr, kprec, dev, clocks):
+    """(1) The substitution pass with kept factors, forward and backward over every level (what each
+    later FP32 application runs): algorithmic bytes = the factor blocks read twice plus the right-hand
+    sides read and written, against the measured HBM bandwidth.  (2) The factorisation of all n_t
+    systems: the plan's flops (8 per complex multiply-add of every front's eliminations) against the
+    ALU peak."""
+    import torch
+
+    kdt = torch.complex128 if kprec == "fp64" else torch.complex64
+    esz = 16 if kprec == "fp64" else 8
+    plan = stfdm.st_space_mf_plan(h.space, 0)
+    tf = _time3(lambda: stfdm.st_spatial_factor(h, kprec))
+    G0 = torch.from_numpy(synth.cn01((pr.n_t, pr.n_x), seed=11)).to(dev).to(kdt)
+    Gw = torch.empty_like(G0)
+    ts = _time3(lambda: stfdm.st_spatial_substitute(h, kprec, G0, Gw))
+    # the substitute call first copies G into W (one read and one write of n_t n_x entries)
+    nbytes = pr.n_t * (2.0 * plan["factor_entries"] * esz + 6.0 * pr.n_x * esz)
+    peaks = measured_peaks() or {}
+    hbm = peaks.get("hbm_gbs", 6800.0)
+    sub = {"bound": "hbm", "kernel": "k_mf_solve_small<32|64> + k_mf_fwd + k_mf_bwd (every level, both directions)",
+           "achieved": nbytes / ts / 1e9, "peak": hbm, "unit": "GB/s", "frac": nbytes / ts / 1e9 / hbm,
+           "traffic": None, "launch_ms": ts * 1e3, "algorithmic_bytes": nbytes,
+           "peak_basis": "measured copy bandwidth (MEASURED_PEAKS.json hbm_gbs)" if "hbm_gbs" in peaks
+           else "fallback 6.8 TB/s"}
+    flops = pr.n_t * plan["flops"]
+    peak, basis = _peak_alu(dev, clocks, kprec)
+    fac = {"bound": "alu", "kernel": "k_mf_factor_small<32|64> + k_mf_factor (every level)",
+           "achieved": flops / tf / 1e12, "peak": peak, "unit": "TFLOP/s", "frac": flops / tf / 1e12 / peak,
+           "launch_ms": tf * 1e3, "peak_basis": basis,
+           "plan": {"fronts": plan["fronts"], "levels": plan["levels"], "max_front": plan["max_front"],
+                    "factor_entries_per_system": plan["factor_entries"], "flops_per_system": plan["flops"]}}
+    return sub, fac
+
+
+def banded_comparison(stfdm, pr, F, p0, psi, tol, etol, kprec, dev, clocks, config, local):
+    """The same mixed solve with the banded spatial solver: one warm-up and one timed step (at the
+    384^2/P2-1024 workload a banded solve takes tens of seconds), its factor roofline, and its error
+    against the multifrontal solution just timed (both refined to the same targets)."""
+    import torch
+
+    t0 = time.perf_counter()
+    hb = stfdm.setup_problem(pr.n, pr.p_t, pr.t_nodes, Lx=pr.Lx, Ly=pr.Ly, device=local, spatial_solver="banded")
+    setup_s = time.perf_counter() - t0
+    out = torch.empty_like(psi)
+    stfdm.st_fdm_solve(hb, F, p0, psi=out, precision="mixed", tol=tol, err_tol=etol)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record()
+    _, info = stfdm.st_fdm_solve(hb, F, p0, psi=out, precision="mixed", tol=tol, err_tol=etol)
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    diff = float(torch.linalg.vector_norm(out - psi) / torch.linalg.vector_norm(psi))
+    roof = banded_roofline(stfdm, hb, pr, kprec, dev, clocks, config)
+    del hb
+    torch.cuda.empty_cache()
+    return {"value": pr.unknowns / (ms * 1e-3), "unit": UNIT, "ms_per_step": ms, "steps": 1, "warmup": 1,
+            "sweeps": info["sweeps"], "restart": info["restart"], "kept_systems": info["kept_systems"],
+            "final_rel_residual": info["rel_residual"], "rel_diff_vs_multifrontal": diff, "setup_s": setup_s,
+            "roofline": roof}
 
 
 # ------------------------------------------------------------------ batched workload

@@ -335,6 +335,15 @@ st_status st_time_transform(st_fdm* h, int which, int precision, const void* in,
  * device arrays (c128 for ST_FP64, c64 for ST_FP32/ST_MIXED); W may alias G. */
 st_status st_spatial_solve(st_fdm* h, int precision, const void* G, void* W, void* stream);
 
+/* Step 3 split in two, for timing and for callers that reuse the factors: st_spatial_factor
+ * factorises all n_t matrices C_k = M_x + s_k A_x and keeps the factors in the handle (banded or
+ * multifrontal, FP64 or FP32; ST_ERR_OOM when they do not fit); st_spatial_substitute then solves
+ * W[k,:] = C_k^{-1} G[k,:] for all k with them (forward and backward substitutions only).  G, W as in
+ * st_spatial_solve (W may alias G).  A later solve of another precision or mode may drop the kept
+ * factors; st_spatial_substitute then fails with ST_ERR_ARG.  Both synchronise the stream (status). */
+st_status st_spatial_factor(st_fdm* h, int precision, void* stream);
+st_status st_spatial_substitute(st_fdm* h, int precision, const void* G, void* W, void* stream);
+
 /* Interpolated load F = (M_t,full (x) M_x) f_nodal (rows t_1.. of the full temporal mass
  * matrix applied to nodal values f at all DOF times t_0, t_1, ...): f_nodal (n_t + 1, n_x) c128,
  * F (n_t, n_x) c128 (device).  Assembly helper, not part of the solve. */

@@ -111,6 +111,8 @@ SIGNATURES = {
     "st_residual_noalloc": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]),
     "st_set_wait_probe": (c_int, [c_void_p, c_double]),
     "st_bs_solve": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]),
+    "st_spatial_factor": (c_int, [c_void_p, c_int, c_void_p]),
+    "st_spatial_substitute": (c_int, [c_void_p, c_int, c_void_p, c_void_p, c_void_p]),
     "st_assemble_mesh": (c_int, [c_int, c_int, c_int, c_void_p, c_int, c_void_p, c_void_p]),
     "st_space_get_mesh": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p,
                                   c_void_p, c_void_p]),

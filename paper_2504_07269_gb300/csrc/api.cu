@@ -1521,6 +1521,42 @@ extern "C" st_status st_spatial_solve(st_fdm* h, int precision, const void* G, v
     return check_status_flag(h, st);
 }
 
+extern "C" st_status st_spatial_factor(st_fdm* h, int precision, void* stream) {
+    if (!h) return fail(ST_ERR_ARG, "st_spatial_factor: NULL argument");
+    if (precision != ST_FP64 && precision != ST_FP32) return fail(ST_ERR_ARG, "st_spatial_factor: FP64 or FP32");
+    DeviceGuard g(h->device);
+    cudaStream_t st = S(stream);
+    release_refinement_workspace(h);
+    const size_t elems = (size_t)h->tm.n_t * h->sm.n_x;
+    const size_t esz = precision == ST_FP64 ? sizeof(double2) : sizeof(float2);
+    // the factorisation runs with its fused (or following) substitutions on a zero right-hand side
+    st_status s = grow(h->ws_big, h->ws_big_bytes, elems * esz, "scratch right-hand side");
+    if (s != ST_OK) return s;
+    CUDA_TRY(cudaMemsetAsync(h->ws_big, 0, elems * esz, st));
+    CUDA_TRY(cudaMemsetAsync(h->ws_status, 0, 2 * sizeof(int), st));
+    h->kept_sys = 0;
+    s = (precision == ST_FP64) ? band_run<double>(h, reinterpret_cast<double2*>(h->ws_big), 1, st)
+                               : band_run<float>(h, reinterpret_cast<float2*>(h->ws_big), 1, st);
+    if (s != ST_OK) return s;
+    return check_status_flag(h, st);
+}
+
+extern "C" st_status st_spatial_substitute(st_fdm* h, int precision, const void* G, void* W, void* stream) {
+    if (!h || !G || !W) return fail(ST_ERR_ARG, "st_spatial_substitute: NULL argument");
+    if (precision != ST_FP64 && precision != ST_FP32) return fail(ST_ERR_ARG, "st_spatial_substitute: FP64 or FP32");
+    const size_t esz = precision == ST_FP64 ? sizeof(double2) : sizeof(float2);
+    if (!h->factors_valid || h->factors_prec != (int)esz || h->kept_sys != 0)
+        return fail(ST_ERR_ARG, "st_spatial_substitute: no kept factors of this precision (call st_spatial_factor)");
+    DeviceGuard g(h->device);
+    cudaStream_t st = S(stream);
+    const size_t elems = (size_t)h->tm.n_t * h->sm.n_x;
+    if (W != G) CUDA_TRY(cudaMemcpyAsync(W, G, elems * esz, cudaMemcpyDeviceToDevice, st));
+    st_status s = (precision == ST_FP64) ? band_run<double>(h, reinterpret_cast<double2*>(W), 2, st)
+                                         : band_run<float>(h, reinterpret_cast<float2*>(W), 2, st);
+    if (s != ST_OK) return s;
+    return check_status_flag(h, st);
+}
+
 extern "C" st_status st_load_nodal(st_fdm* h, const void* f_nodal, void* F, void* stream) {
     if (!h || !f_nodal || !F) return fail(ST_ERR_ARG, "st_load_nodal: NULL argument");
     if (h->tm.n_t > 65535) return fail(ST_ERR_UNSUPPORTED, "st_load_nodal: n_t > 65535");

@@ -427,6 +427,25 @@ def st_spatial_solve(h: FdmHandle, precision: str, G, W=None, stream=None):
     return W
 
 
+def st_spatial_factor(h: FdmHandle, precision: str, stream=None):
+    """Factorise all n_t spatial matrices and keep the factors in the handle."""
+    if precision not in ("fp64", "fp32"):
+        raise ValueError("precision must be fp64 or fp32")
+    check(lib().st_spatial_factor(h.ptr, PREC[precision], _stream(stream)), "st_spatial_factor")
+
+
+def st_spatial_substitute(h: FdmHandle, precision: str, G, W=None, stream=None):
+    """W[k,:] = C_k^{-1} G[k,:] with the factors kept by st_spatial_factor."""
+    dt = _dtype(precision)
+    _check_st(h, G, dt, "G")
+    if W is None:
+        W = torch.empty_like(G)
+    _check_st(h, W, dt, "W")
+    check(lib().st_spatial_substitute(h.ptr, PREC[precision], _ptr(G), _ptr(W), _stream(stream)),
+          "st_spatial_substitute")
+    return W
+
+
 def st_load_nodal(h: FdmHandle, f_nodal, F=None, stream=None):
     if not f_nodal.is_cuda or f_nodal.dtype != torch.complex128 or tuple(f_nodal.shape) != (h.n_t + 1, h.n_x):
         raise ValueError("f_nodal: expected a CUDA complex128 tensor of shape (n_t + 1, n_x)")

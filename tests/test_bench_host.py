@@ -86,6 +86,10 @@ def test_recorded_traffic_is_keyed_on_kernel_source(tmp_path, monkeypatch):
     dev = (csrc / "device.cuh").read_text()
     (csrc / "device.cuh").write_text(dev.replace("struct st_fdm {", "struct st_fdm {\n    int host_only_field = 0;", 1))
     assert bench.profiled_traffic("c3") == 1.0e12             # host bookkeeping only
+    dev = (csrc / "device.cuh").read_text()
+    (csrc / "device.cuh").write_text(dev.replace("struct BandArgs {", "struct BandArgs {\n    int extra;", 1))
+    assert bench.profiled_traffic("c3") is None               # the banded kernels' arguments changed
+    (csrc / "device.cuh").write_text(dev)
     sub = (csrc / "k_subst.cu").read_text()
     (csrc / "k_subst.cu").write_text(sub + "\n// edited\n")
     assert bench.profiled_traffic("c3") is None               # kernel source changed

@@ -162,3 +162,22 @@ def test_mesh_handle_rejects_structured_only_calls(dev):
         stfdm.setup_mesh_problem(2, 1, coords, cells, 1, synth.uniform_time_nodes(4, 1.0), device=0,
                                  spatial_solver="banded")
     assert e.value.status == _lib.ST_ERR_UNSUPPORTED
+
+
+@pytest.mark.parametrize("solver", ["banded", "multifrontal"])
+def test_factor_then_substitute_equals_spatial_solve(dev, solver):
+    """st_spatial_factor + st_spatial_substitute (the kept factors applied twice to different right-hand
+    sides) give what st_spatial_solve gives, FP32 and FP64."""
+    from paper_2504_07269_gb300 import _lib, stfdm
+
+    h = stfdm.setup_problem(37, 2, synth.uniform_time_nodes(5, 0.7), device=0, spatial_solver=solver)
+    for prec, dt, bar in (("fp32", torch.complex64, 1e-6), ("fp64", torch.complex128, 1e-13)):
+        with pytest.raises(_lib.StfdmError):
+            stfdm.st_spatial_substitute(h, prec, torch.zeros((h.n_t, h.n_x), dtype=dt, device=dev))
+        stfdm.st_spatial_factor(h, prec)
+        for seed in (1, 2):
+            G = torch.from_numpy(synth.cn01((h.n_t, h.n_x), seed=seed)).to(dev).to(dt)
+            W1 = stfdm.st_spatial_substitute(h, prec, G)
+            W2 = stfdm.st_spatial_solve(h, prec, G.clone())
+            stfdm.st_spatial_factor(h, prec)   # st_spatial_solve's transient factors replaced the kept ones
+            assert rel(W1.cpu().numpy(), W2.cpu().numpy()) <= bar, (prec, seed)
