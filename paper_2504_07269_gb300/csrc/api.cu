@@ -841,6 +841,7 @@ st_status solve_mixed_gmres(st_fdm* h, bool adjoint, const void* F, const void* 
     double bnorm = -1, rel = -1, err_est = -1;
     double cur_tol = tol;
     bool converged = false, first = true, x_zero = true;
+    bool z0_ready = false;   // Z_0 = FDM32(V_0) of the current residual, left by a failed error estimate
     std::vector<cd> H((size_t)(m + 1) * m), g(m + 1), sn(m);
     std::vector<double> cs(m);
     std::vector<double2> hh(3 * MV);
@@ -876,8 +877,10 @@ st_status solve_mixed_gmres(st_fdm* h, bool adjoint, const void* F, const void* 
                 converged = true;
                 break;
             }
-            // lower the residual target by the factor the estimate is off, and keep iterating
+            // lower the residual target by the factor the estimate is off, and keep iterating; the next
+            // cycle starts from this residual, whose preconditioned direction is already in Z_0
             cur_tol = std::max(1e-16, std::min(0.5 * rel, rel * (0.5 * o.err_tol / err_est)));
+            z0_ready = true;
             continue;
         }
         if (its >= maxit) break;
@@ -886,9 +889,13 @@ st_status solve_mixed_gmres(st_fdm* h, bool adjoint, const void* F, const void* 
         g[0] = beta;
         int jdone = 0;
         for (int j = 0; j < m; ++j) {
-            s = precond32(h, adjoint, Vp(j), Zp(j), keep, first, scal + 4, st);
-            if (s != ST_OK) return s;
-            ++its;
+            if (j == 0 && z0_ready) {
+                z0_ready = false;   // same iterate, same residual, same V_0: reuse its FDM32 application
+            } else {
+                s = precond32(h, adjoint, Vp(j), Zp(j), keep, first, scal + 4, st);
+                if (s != ST_OK) return s;
+                ++its;
+            }
             // w = K z_j (operator apply: no right-hand side)
             CUDA_TRY(launch_residual(h->sm, n_t, time_band(h), h->dt.Mb, Bband, bsign, nullptr, nullptr, h->dt.m, Zp(j), nullptr,
                                      w, parts, scal, st));

@@ -426,12 +426,26 @@ k_mf_solve_small(MfArgs<T> a, int nfronts, int nsys, int fwd) {
     const int np = fr.np, nu = fr.nu, f = np + nu;
     const C<T>* Fp = a.fac + (size_t)(a.fac_keep ? k : ks) * a.fac_stride + fr.foff;
     C<T>* g = a.rhs + (size_t)k * a.n;
-    for (int c = 0; c < np; ++c)
+    // stage the factor block: consecutive lanes read consecutive entries of the column-major block,
+    // four independent loads in flight per lane
+    {
+        const int tot = f * np;
+        for (int base = 0; base < tot; base += 128) {
+            C<T> v[4];
+            int idx[4];
 #pragma unroll
-        for (int i = 0; i < R; ++i) {
-            const int r = lane + 32 * i;
-            if (r >= c && r < f) L[tri_row(r) + c] = Fp[(size_t)c * f + r];
+            for (int u = 0; u < 4; ++u) {
+                idx[u] = base + 32 * u + lane;
+                v[u] = idx[u] < tot ? Fp[idx[u]] : mk<T>(0, 0);
+            }
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                if (idx[u] >= tot) continue;
+                const int c = idx[u] / f, r = idx[u] - c * f;
+                if (r >= c) L[tri_row(r) + c] = v[u];
+            }
         }
+    }
     if (fwd) {
         C<T>* uv = a.uvec + (size_t)ks * a.uvec_stride;
 #pragma unroll
