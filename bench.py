@@ -443,7 +443,7 @@ def run_ours(args):
     # ---- the banded solver (the fixed spatial design) on the same workload, for comparison
     banded = None
     if args.spatial == "multifrontal" and args.compare_banded and args.precision == "mixed":
-        del h
+        h.close()      # release the multifrontal handle's factors and workspace before the banded solver's
         torch.cuda.empty_cache()
         banded = banded_comparison(stfdm, pr, F, p0, psi, tol, etol, kprec, dev, clocks, args.config, local)
 
@@ -592,7 +592,7 @@ def banded_comparison(stfdm, pr, F, p0, psi, tol, etol, kprec, dev, clocks, conf
     ms = e0.elapsed_time(e1)
     diff = float(torch.linalg.vector_norm(out - psi) / torch.linalg.vector_norm(psi))
     roof = banded_roofline(stfdm, hb, pr, kprec, dev, clocks, config)
-    del hb
+    hb.close()
     torch.cuda.empty_cache()
     return {"value": pr.unknowns / (ms * 1e-3), "unit": UNIT, "ms_per_step": ms, "steps": 1, "warmup": 1,
             "sweeps": info["sweeps"], "restart": info["restart"], "kept_systems": info["kept_systems"],

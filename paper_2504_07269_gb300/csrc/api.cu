@@ -311,7 +311,7 @@ st_status mf_run(st_fdm* h, C<T>* G, int mode, cudaStream_t st) {
     const MfPlan& P = h->mf;
     const int n_t = h->tm.n_t;
     const size_t esz = sizeof(C<T>);
-    if (mode == 2 && (!h->factors_valid || h->factors_prec != (int)esz))
+    if (mode == 2 && (!h->factors_valid || h->factors_prec != (int)sizeof(T)))
         return fail(ST_ERR_ARG, "spatial solve: no stored factors");
     size_t freeb = 0, total = 0;
     CUDA_TRY(cudaMemGetInfo(&freeb, &total));
@@ -353,7 +353,7 @@ st_status mf_run(st_fdm* h, C<T>* G, int mode, cudaStream_t st) {
     }
     if (mode == 1) {
         h->factors_valid = 1;
-        h->factors_prec = (int)esz;
+        h->factors_prec = (int)sizeof(T);   // the real type's size, as for banded factors
     }
     return ST_OK;
 }
@@ -1552,7 +1552,7 @@ extern "C" st_status st_spatial_substitute(st_fdm* h, int precision, const void*
     if (!h || !G || !W) return fail(ST_ERR_ARG, "st_spatial_substitute: NULL argument");
     if (precision != ST_FP64 && precision != ST_FP32) return fail(ST_ERR_ARG, "st_spatial_substitute: FP64 or FP32");
     const size_t esz = precision == ST_FP64 ? sizeof(double2) : sizeof(float2);
-    if (!h->factors_valid || h->factors_prec != (int)esz || h->kept_sys != 0)
+    if (!h->factors_valid || h->factors_prec != (int)(esz / 2) || h->kept_sys != 0)
         return fail(ST_ERR_ARG, "st_spatial_substitute: no kept factors of this precision (call st_spatial_factor)");
     DeviceGuard g(h->device);
     cudaStream_t st = S(stream);

@@ -25,13 +25,17 @@ class _Handle:
     def __init__(self, ptr):
         self.ptr = ptr
 
-    def __del__(self):
+    def close(self):
+        """Destroy the library object now (its device memory is released); the handle is unusable after."""
         if self.ptr and self._destroy:
             try:
                 getattr(lib(), self._destroy)(self.ptr)
             except Exception:
                 pass
-            self.ptr = None
+        self.ptr = None
+
+    def __del__(self):
+        self.close()
 
 
 class TimeHandle(_Handle):
