@@ -409,45 +409,46 @@ __global__ void __launch_bounds__(SmallCfg<T, FM>::W * 32) k_mf_factor_small(MfA
         }
 }
 
+// Substitutions for fronts with f <= FM: one warp per (front, system), the front vector in registers
+// (lane l holds rows l, l + 32, ...), the pivot value of each step broadcast by a shuffle from its
+// owner, the factor entries read straight from global memory (column q of the block is contiguous,
+// so a step's loads are coalesced; they do not depend on the chain and are issued ahead of it).
+// Shared memory only gathers the children's update vectors (forward).
 template <typename T, int FM>
-__global__ void __launch_bounds__(SmallCfg<T, FM>::W * 32)
+struct SolveSmallCfg {
+    static constexpr int R = FM / 32;
+    static constexpr int W = 8;
+    static constexpr size_t SMEM = sizeof(C<T>) * (size_t)W * FM;
+};
+
+template <typename T, int R>
+__device__ __forceinline__ C<T> row_value(const C<T> (&v)[R], int q) {
+    C<T> src = v[0];
+#pragma unroll
+    for (int i = 1; i < R; ++i)
+        if ((q >> 5) == i) src = v[i];
+    return shfl_c<T>(src, q & 31);
+}
+
+template <typename T, int FM>
+__global__ void __launch_bounds__(SolveSmallCfg<T, FM>::W * 32)
 k_mf_solve_small(MfArgs<T> a, int nfronts, int nsys, int fwd) {
-    using Cfg = SmallCfg<T, FM>;
-    constexpr int R = Cfg::R;
+    using Cfg = SolveSmallCfg<T, FM>;
+    constexpr int R = Cfg::R, PF = 8;   // steps whose factor entries are loaded ahead
     extern __shared__ __align__(16) unsigned char mf_smem[];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const long long item = (long long)blockIdx.x * Cfg::W + warp;
     if (item >= (long long)nfronts * nsys) return;
     const int fi = (int)(item / nsys), ks = (int)(item - (long long)fi * nsys);
-    C<T>* L = reinterpret_cast<C<T>*>(mf_smem) + (size_t)warp * Cfg::TILE;  // the factor block, packed rows
-    C<T>* x = L + FM * (FM + 1) / 2;                                           // [FM]
     const MfFrontDev fr = a.fronts[a.level_fronts[a.lvl_off + fi]];
     const int k = a.k0 + ks;
     const int np = fr.np, nu = fr.nu, f = np + nu;
     const C<T>* Fp = a.fac + (size_t)(a.fac_keep ? k : ks) * a.fac_stride + fr.foff;
     C<T>* g = a.rhs + (size_t)k * a.n;
-    // stage the factor block: consecutive lanes read consecutive entries of the column-major block,
-    // four independent loads in flight per lane
-    {
-        const int tot = f * np;
-        for (int base = 0; base < tot; base += 128) {
-            C<T> v[4];
-            int idx[4];
-#pragma unroll
-            for (int u = 0; u < 4; ++u) {
-                idx[u] = base + 32 * u + lane;
-                v[u] = idx[u] < tot ? Fp[idx[u]] : mk<T>(0, 0);
-            }
-#pragma unroll
-            for (int u = 0; u < 4; ++u) {
-                if (idx[u] >= tot) continue;
-                const int c = idx[u] / f, r = idx[u] - c * f;
-                if (r >= c) L[tri_row(r) + c] = v[u];
-            }
-        }
-    }
+    C<T> v[R];
     if (fwd) {
         C<T>* uv = a.uvec + (size_t)ks * a.uvec_stride;
+        C<T>* x = reinterpret_cast<C<T>*>(mf_smem) + (size_t)warp * FM;
 #pragma unroll
         for (int i = 0; i < R; ++i) {
             const int r = lane + 32 * i;
@@ -458,54 +459,80 @@ k_mf_solve_small(MfArgs<T> a, int nfronts, int nsys, int fwd) {
             const MfFrontDev ch = a.fronts[a.children[fr.child_off + ci]];
             const int* rp = a.relpos + ch.relpos_off;
             for (int t = lane; t < ch.nu; t += 32) {
-                const C<T> v = uv[ch.uvoff + t];
+                const C<T> u = uv[ch.uvoff + t];
                 C<T>& d = x[rp[t]];
-                d.x += v.x;
-                d.y += v.y;
-            }
-            __syncwarp();
-        }
-        for (int q = 0; q < np; ++q) {
-            const C<T> z = x[q];
-#pragma unroll
-            for (int i = 0; i < R; ++i) {
-                const int r = lane + 32 * i;
-                if (r > q && r < f) cfms<T>(x[r], L[tri_row(r) + q], z);
+                d.x += u.x;
+                d.y += u.y;
             }
             __syncwarp();
         }
 #pragma unroll
         for (int i = 0; i < R; ++i) {
             const int r = lane + 32 * i;
-            if (r < np) g[a.perm[fr.first + r]] = cmul<T>(x[r], cinv<T>(L[tri_row(r) + r]));
-            else if (r < f) uv[fr.uvoff + r - np] = x[r];
+            v[i] = r < f ? x[r] : mk<T>(0, 0);
+        }
+        for (int q0 = 0; q0 < np; q0 += PF) {
+            C<T> Lq[PF][R];
+#pragma unroll
+            for (int u = 0; u < PF; ++u)
+#pragma unroll
+                for (int i = 0; i < R; ++i) {
+                    const int q = q0 + u, r = lane + 32 * i;
+                    Lq[u][i] = (q < np && r > q && r < f) ? Fp[(size_t)q * f + r] : mk<T>(0, 0);
+                }
+#pragma unroll
+            for (int u = 0; u < PF; ++u) {
+                const int q = q0 + u;
+                if (q >= np) break;
+                const C<T> z = row_value<T, R>(v, q);
+#pragma unroll
+                for (int i = 0; i < R; ++i) cfms<T>(v[i], Lq[u][i], z);   // zero entries above the step
+            }
+        }
+#pragma unroll
+        for (int i = 0; i < R; ++i) {
+            const int r = lane + 32 * i;
+            if (r < np) g[a.perm[fr.first + r]] = cmul<T>(v[i], cinv<T>(Fp[(size_t)r * f + r]));
+            else if (r < f) uv[fr.uvoff + r - np] = v[i];
         }
     } else {
 #pragma unroll
         for (int i = 0; i < R; ++i) {
             const int r = lane + 32 * i;
-            if (r < f) x[r] = g[a.perm[r < np ? fr.first + r : a.urows[fr.urows_off + r - np]]];
+            v[i] = r < f ? g[a.perm[r < np ? fr.first + r : a.urows[fr.urows_off + r - np]]] : mk<T>(0, 0);
         }
-        __syncwarp();
-        for (int q = np - 1; q >= 0; --q) {
-            C<T> acc = mk<T>(0, 0);
+        for (int q1 = np; q1 > 0; q1 -= PF) {
+            C<T> Lq[PF][R];
 #pragma unroll
-            for (int i = 0; i < R; ++i) {
-                const int r = lane + 32 * i;
-                if (r > q && r < f) cfma<T>(acc, L[tri_row(r) + q], x[r]);
-            }
+            for (int u = 0; u < PF; ++u)
 #pragma unroll
-            for (int off = 16; off > 0; off >>= 1) {
-                acc.x += __shfl_xor_sync(0xffffffffu, acc.x, off);
-                acc.y += __shfl_xor_sync(0xffffffffu, acc.y, off);
+                for (int i = 0; i < R; ++i) {
+                    const int q = q1 - 1 - u, r = lane + 32 * i;
+                    Lq[u][i] = (q >= 0 && r > q && r < f) ? Fp[(size_t)q * f + r] : mk<T>(0, 0);
+                }
+#pragma unroll
+            for (int u = 0; u < PF; ++u) {
+                const int q = q1 - 1 - u;
+                if (q < 0) break;
+                C<T> acc = mk<T>(0, 0);
+#pragma unroll
+                for (int i = 0; i < R; ++i) cfma<T>(acc, Lq[u][i], v[i]);
+#pragma unroll
+                for (int off = 16; off > 0; off >>= 1) {
+                    acc.x += __shfl_xor_sync(0xffffffffu, acc.x, off);
+                    acc.y += __shfl_xor_sync(0xffffffffu, acc.y, off);
+                }
+                if (lane == (q & 31)) {
+#pragma unroll
+                    for (int i = 0; i < R; ++i)
+                        if ((q >> 5) == i) v[i] = csub<T>(v[i], acc);
+                }
             }
-            if (lane == 0) x[q] = csub<T>(x[q], acc);
-            __syncwarp();
         }
 #pragma unroll
         for (int i = 0; i < R; ++i) {
             const int r = lane + 32 * i;
-            if (r < np) g[a.perm[fr.first + r]] = x[r];
+            if (r < np) g[a.perm[fr.first + r]] = v[i];
         }
     }
 }
@@ -524,9 +551,10 @@ cudaError_t mf_small_launch(MfArgs<T> a, int lvl_off, int nfronts, int nsys, int
         if (e != cudaSuccess) return e;
         k_mf_factor_small<T, FM><<<(unsigned)blocks, Cfg::W * 32, Cfg::SMEM, st>>>(a, nfronts, nsys);
     } else {
-        e = cudaFuncSetAttribute(k_mf_solve_small<T, FM>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Cfg::SMEM);
-        if (e != cudaSuccess) return e;
-        k_mf_solve_small<T, FM><<<(unsigned)blocks, Cfg::W * 32, Cfg::SMEM, st>>>(a, nfronts, nsys, what == 1 ? 1 : 0);
+        using SCfg = SolveSmallCfg<T, FM>;
+        const long long sblocks = (items + SCfg::W - 1) / SCfg::W;
+        if (sblocks > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
+        k_mf_solve_small<T, FM><<<(unsigned)sblocks, SCfg::W * 32, SCfg::SMEM, st>>>(a, nfronts, nsys, what == 1 ? 1 : 0);
     }
     note_launches(1);
     return cudaGetLastError();
