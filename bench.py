@@ -66,6 +66,9 @@ def parse_args(argv=None):
                     help="set up, then run exactly one solve and exit (for ncu launch lists)")
     ap.add_argument("--profile-xform", action="store_true",
                     help="set up, then run one tensor-core forward time transform and exit (small device footprint)")
+    ap.add_argument("--profile-mf", action="store_true",
+                    help="set up, then run one multifrontal FP32 factorisation of all systems and one substitution "
+                         "pass with the kept factors, and exit (for ncu captures of those kernels)")
     return ap.parse_args(argv)
 
 
@@ -157,40 +160,49 @@ def measured_peaks():
     return None
 
 
-def kernel_source_sha():
-    """Hash of the source of the kernels the FP32 banded spatial solve runs (the blocked-panel factor
-    kernel's section of k_band.cu, the substitution kernels, the asynchronous-copy helpers, and the
-    complex helpers and launch arguments of the device header): the recorded DRAM traffic is used
-    only while this is unchanged."""
+def kernel_source_sha(kind: str = "band"):
+    """Hash of the source of the kernels whose DRAM traffic was recorded: for "band" the FP32 banded
+    spatial solve (the blocked-panel factor kernel's section of k_band.cu, the substitution kernels,
+    the asynchronous-copy helpers, and the complex helpers and launch arguments of the device header);
+    for "mf" the multifrontal kernels (k_mf.cu, the complex helpers and the front/launch-argument
+    structs of the device header).  The recorded traffic is used only while this is unchanged."""
     csrc = os.path.join(ROOT, "paper_2504_07269_gb300", "csrc")
+    with open(os.path.join(csrc, "device.cuh")) as fh:
+        dev = fh.read()
+    helpers = dev[dev.index("// ------------------------------------------------------------------ complex helpers"):
+                  dev.index("// ------------------------------------------------------------------ handle")]
+    if kind == "mf":
+        with open(os.path.join(csrc, "k_mf.cu")) as fh:
+            h = hashlib.sha256(fh.read().encode())
+        a = dev.index("struct MfFrontDev {")
+        b = dev.index("\n};", dev.index("struct MfArgs {")) + 3
+        h.update((helpers + dev[a:b]).encode())
+        return h.hexdigest()[:16]
     with open(os.path.join(csrc, "k_band.cu")) as fh:
         text = fh.read()
     start = text.index("// ------------------------------------------------------------------ complex64, blocked panel")
     end = text.index("// ------------------------------------------------------------------ backward substitution by one CTA")
     h = hashlib.sha256(text[start:end].encode())
-    for name in ("k_subst.cu", "async.cuh", "device.cuh"):
+    for name in ("k_subst.cu", "async.cuh"):
         with open(os.path.join(csrc, name)) as fh:
-            part = fh.read()
-        if name == "device.cuh":   # only what the banded kernels consume: the complex helpers, BandArgs
-            a = part.index("// ------------------------------------------------------------------ complex helpers")
-            b = part.index("// ------------------------------------------------------------------ handle")
-            c = part.index("struct BandArgs {")
-            part = part[a:b] + part[c:part.index("\n};", c) + 3]
-        h.update(part.encode())
+            h.update(fh.read().encode())
+    c = dev.index("struct BandArgs {")
+    h.update((helpers + dev[c:dev.index("\n};", c) + 3]).encode())
     return h.hexdigest()[:16]
 
 
-def profiled_traffic(config: str):
-    """DRAM bytes of one FP32 spatial solve (factorisation with the fused forward substitution,
-    then the backward substitution) from the committed ncu summary, or None if the kernels' source
-    changed since the capture."""
+def profiled_traffic(key: str, kind: str = "band"):
+    """DRAM bytes per launch of the kernels named by key (e.g. band_factor_fp32_c3: one FP32 banded
+    spatial solve, the factorisation with the fused forward substitution, then the backward
+    substitution) from the committed ncu summary, or None if the kernels' source changed since the
+    capture."""
     p = os.path.join(ROOT, "profiles", "traffic.json")
     if not os.path.exists(p):
         return None
     with open(p) as fh:
         d = json.load(fh)
-    e = d.get(f"band_factor_fp32_{config}")
-    if not e or e.get("k_band_sha") != kernel_source_sha():
+    e = d.get(key)
+    if not e or e.get("src_sha", e.get("k_band_sha")) != kernel_source_sha(kind):
         return None
     return e.get("dram_bytes_per_launch")
 
@@ -330,6 +342,14 @@ def run_ours(args):
         if rank == 0:
             print(json.dumps({"profile_xform": args.config, "norm": float(torch.linalg.vector_norm(G32))}))
         return 0
+    if args.profile_mf:
+        G = F.to(torch.complex64) + torch.from_numpy(synth.cn01((pr.n_t, pr.n_x), seed=11)).to(dev).to(torch.complex64)
+        stfdm.st_spatial_factor(h, "fp32")
+        W = stfdm.st_spatial_substitute(h, "fp32", G)
+        torch.cuda.synchronize()
+        if rank == 0:
+            print(json.dumps({"profile_mf": args.config, "norm": float(torch.linalg.vector_norm(W))}))
+        return 0
     if args.profile_step:
         _, info = stfdm.st_fdm_solve(h, F, p0, psi=psi, precision=args.precision, tol=tol, err_tol=etol)
         torch.cuda.synchronize()
@@ -436,7 +456,7 @@ def run_ours(args):
     # HBM) and its factorisation (ALU), or the banded factor-and-solve (ALU)
     kprec = "fp64" if args.precision == "fp64" else "fp32"
     if args.spatial == "multifrontal":
-        roof, roof_factor = multifrontal_rooflines(stfdm, h, pr, kprec, dev, clocks)
+        roof, roof_factor = multifrontal_rooflines(stfdm, h, pr, kprec, dev, clocks, args.config)
     else:
         roof, roof_factor = banded_roofline(stfdm, h, pr, kprec, dev, clocks, args.config), None
 
@@ -534,11 +554,11 @@ def banded_roofline(stfdm, h, pr, kprec, dev, clocks, config):
     kname = ("k_band_factor_v4 (complex64, fused forward substitution) + k_subst_bwd<float>" if kprec == "fp32"
              else "k_band_factor_solve<double,32> + k_subst_bwd<double>")
     return {"bound": "alu", "kernel": kname, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-            "frac": achieved / peak, "traffic": profiled_traffic(config), "launch_ms": tk * 1e3,
+            "frac": achieved / peak, "traffic": profiled_traffic(f"band_factor_fp32_{config}"), "launch_ms": tk * 1e3,
             "peak_basis": basis}
 
 
-def multifrontal_rooflines(stfdm, h, pr, kprec, dev, clocks):
+def multifrontal_rooflines(stfdm, h, pr, kprec, dev, clocks, config):
     """(1) The substitution pass with kept factors, forward and backward over every level (what each
     later FP32 application runs): algorithmic bytes = the factor blocks read twice plus the right-hand
     sides read and written, against the measured HBM bandwidth.  (2) The factorisation of all n_t
@@ -559,14 +579,16 @@ def multifrontal_rooflines(stfdm, h, pr, kprec, dev, clocks):
     hbm = peaks.get("hbm_gbs", 6800.0)
     sub = {"bound": "hbm", "kernel": "k_mf_solve_small<32|64> + k_mf_fwd + k_mf_bwd (every level, both directions)",
            "achieved": nbytes / ts / 1e9, "peak": hbm, "unit": "GB/s", "frac": nbytes / ts / 1e9 / hbm,
-           "traffic": None, "launch_ms": ts * 1e3, "algorithmic_bytes": nbytes,
+           "traffic": profiled_traffic(f"mf_subst_{kprec}_{config}", "mf"), "launch_ms": ts * 1e3,
+           "algorithmic_bytes": nbytes,
            "peak_basis": "measured copy bandwidth (MEASURED_PEAKS.json hbm_gbs)" if "hbm_gbs" in peaks
            else "fallback 6.8 TB/s"}
     flops = pr.n_t * plan["flops"]
     peak, basis = _peak_alu(dev, clocks, kprec)
     fac = {"bound": "alu", "kernel": "k_mf_factor_small<32|64> + k_mf_factor (every level)",
            "achieved": flops / tf / 1e12, "peak": peak, "unit": "TFLOP/s", "frac": flops / tf / 1e12 / peak,
-           "launch_ms": tf * 1e3, "peak_basis": basis,
+           "traffic": profiled_traffic(f"mf_factor_{kprec}_{config}", "mf"), "launch_ms": tf * 1e3,
+           "peak_basis": basis,
            "plan": {"fronts": plan["fronts"], "levels": plan["levels"], "max_front": plan["max_front"],
                     "factor_entries_per_system": plan["factor_entries"], "flops_per_system": plan["flops"]}}
     return sub, fac

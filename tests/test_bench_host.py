@@ -75,21 +75,29 @@ def test_recorded_traffic_is_keyed_on_kernel_source(tmp_path, monkeypatch):
     csrc = root / "paper_2504_07269_gb300" / "csrc"
     csrc.mkdir(parents=True)
     src = os.path.join(ROOT, "paper_2504_07269_gb300", "csrc")
-    for name in ("k_band.cu", "k_subst.cu", "async.cuh", "device.cuh"):
+    for name in ("k_band.cu", "k_subst.cu", "async.cuh", "device.cuh", "k_mf.cu"):
         shutil.copy(os.path.join(src, name), csrc / name)
     (root / "profiles").mkdir()
     monkeypatch.setattr(bench, "ROOT", str(root))
-    rec = {"band_factor_fp32_c3": {"k_band_sha": bench.kernel_source_sha(), "dram_bytes_per_launch": 1.0e12}}
+    rec = {"band_factor_fp32_c3": {"k_band_sha": bench.kernel_source_sha(), "dram_bytes_per_launch": 1.0e12},
+           "mf_subst_fp32_c3": {"src_sha": bench.kernel_source_sha("mf"), "dram_bytes_per_launch": 2.0e11}}
     (root / "profiles" / "traffic.json").write_text(json.dumps(rec))
-    assert bench.profiled_traffic("c3") == 1.0e12
-    assert bench.profiled_traffic("c2") is None               # no capture of that workload
+    assert bench.profiled_traffic("band_factor_fp32_c3") == 1.0e12
+    assert bench.profiled_traffic("band_factor_fp32_c2") is None      # no capture of that workload
+    assert bench.profiled_traffic("mf_subst_fp32_c3", "mf") == 2.0e11
+    assert bench.profiled_traffic("mf_subst_fp32_c3") is None         # recorded against the multifrontal source
+    mf = (csrc / "k_mf.cu").read_text()
+    (csrc / "k_mf.cu").write_text(mf + "\n// edited\n")
+    assert bench.profiled_traffic("mf_subst_fp32_c3", "mf") is None   # multifrontal source changed
+    assert bench.profiled_traffic("band_factor_fp32_c3") == 1.0e12    # the banded record is unaffected
+    (csrc / "k_mf.cu").write_text(mf)
     dev = (csrc / "device.cuh").read_text()
     (csrc / "device.cuh").write_text(dev.replace("struct st_fdm {", "struct st_fdm {\n    int host_only_field = 0;", 1))
-    assert bench.profiled_traffic("c3") == 1.0e12             # host bookkeeping only
+    assert bench.profiled_traffic("band_factor_fp32_c3") == 1.0e12             # host bookkeeping only
     dev = (csrc / "device.cuh").read_text()
     (csrc / "device.cuh").write_text(dev.replace("struct BandArgs {", "struct BandArgs {\n    int extra;", 1))
-    assert bench.profiled_traffic("c3") is None               # the banded kernels' arguments changed
+    assert bench.profiled_traffic("band_factor_fp32_c3") is None               # the banded kernels' arguments changed
     (csrc / "device.cuh").write_text(dev)
     sub = (csrc / "k_subst.cu").read_text()
     (csrc / "k_subst.cu").write_text(sub + "\n// edited\n")
-    assert bench.profiled_traffic("c3") is None               # kernel source changed
+    assert bench.profiled_traffic("band_factor_fp32_c3") is None               # kernel source changed
