@@ -132,13 +132,16 @@ typedef struct {
     double rel_error_estimate;   /* ST_MIXED with GMRES and err_tol > 0: the last ||FDM32(R)|| / ||psi_hat|| (-1 otherwise) */
     int kept_systems;            /* ST_MIXED: spatial systems whose factors stayed in memory across
                                     applications (n_t when all were kept, 0 when none) */
+    int reorth_steps;            /* ST_MIXED with GMRES: Arnoldi steps whose Gram-Schmidt pass was
+                                    repeated (the first removed more than half of the new vector's
+                                    norm squared); 0 in batched solves, which always run two passes */
 } st_solve_info;
 
 /* ------------------------------------------------------------------ status */
 const char* st_status_string(st_status s);
 const char* st_last_error_message(void);
 int st_abi_version(void);   /* returns STFDM_ABI_VERSION of the built library */
-#define STFDM_ABI_VERSION 7
+#define STFDM_ABI_VERSION 8
 
 /* ------------------------------------------------------------------ assembly (host) */
 /* Temporal matrices of eq. (matrix_t), Section 3.  p_t in {1, 2}: continuous piecewise

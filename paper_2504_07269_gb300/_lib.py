@@ -57,7 +57,8 @@ class st_solve_info(ctypes.Structure):
     _fields_ = [("sweeps", c_int), ("factors_kept", c_int), ("rel_residual", c_double),
                 ("residual_history", c_double * 16), ("kappa_x", c_double), ("min_neg_im_shift", c_double),
                 ("setup_seconds", c_double), ("tensor_cores", c_int), ("kernel_launches", c_int),
-                ("restart", c_int), ("rel_error_estimate", c_double), ("kept_systems", c_int)]
+                ("restart", c_int), ("rel_error_estimate", c_double), ("kept_systems", c_int),
+                ("reorth_steps", c_int)]
 
 
 class st_batch_opts(ctypes.Structure):

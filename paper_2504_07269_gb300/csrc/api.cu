@@ -38,6 +38,10 @@ cudaError_t launch_multidot(const double2* const* Vdev, int nv, const double2* w
 cudaError_t launch_multiaxpy(const double2* const* Vdev, int nv, const double2* c, double sign, double2* y, size_t n,
                              cudaStream_t st);
 cudaError_t launch_scale(const double2* x, double alpha, double2* y, size_t n, cudaStream_t st);
+cudaError_t launch_gs_project(const double2* const* Vdev, int nv, int shift, const double2* w, size_t n,
+                              double2* partial, double2* out, cudaStream_t st);
+cudaError_t launch_gs_update(const double2* const* Vdev, int nv, int shift, const double2* c, double2* w, size_t n,
+                             double2* partial, double2* out, cudaStream_t st);
 cudaError_t launch_set_scalars(double* dst, double a, double b, cudaStream_t st);
 cudaError_t launch_bs_accum(int n_t, int n_x, int l, const double2* T, double2* W, cudaStream_t st);
 int krylov_partial_count();
@@ -837,7 +841,7 @@ st_status solve_mixed_gmres(st_fdm* h, bool adjoint, const void* F, const void* 
     CUDA_TRY(cudaMemcpyAsync(const_cast<double2**>(P) + 2 * m + 2, &x, sizeof(double2*), cudaMemcpyHostToDevice, st));
     double hist[16];
     int nh = 0;
-    int its = 0;
+    int its = 0, reorth = 0;
     double bnorm = -1, rel = -1, err_est = -1;
     double cur_tol = tol;
     bool converged = false, first = true, x_zero = true;
@@ -899,18 +903,28 @@ st_status solve_mixed_gmres(st_fdm* h, bool adjoint, const void* F, const void* 
             // w = K z_j (operator apply: no right-hand side)
             CUDA_TRY(launch_residual(h->sm, n_t, time_band(h), h->dt.Mb, Bband, bsign, nullptr, nullptr, h->dt.m, Zp(j), nullptr,
                                      w, parts, scal, st));
-            // two passes of classical Gram-Schmidt, then ||w||: with a good preconditioner w = K z_j
-            // is close to v_j, so the first pass removes nearly all of it and the second is always needed
-            CUDA_TRY(launch_multidot(P, j + 1, w, N, partial, hb, st));
-            CUDA_TRY(launch_multiaxpy(P, j + 1, hb, -1.0, w, N, st));
-            CUDA_TRY(launch_multidot(P, j + 1, w, N, partial, hb + MV, st));
-            CUDA_TRY(launch_multiaxpy(P, j + 1, hb + MV, -1.0, w, N, st));
-            CUDA_TRY(launch_multidot(P + 2 * m + 1, 1, w, N, partial, hb + 2 * MV, st));
+            // Classical Gram-Schmidt on d = w - v_j, h = e_j + V^H d: with the FP32-FDM preconditioner
+            // w = K z_j is close to v_j, and orthogonalising the small difference d instead of w keeps
+            // the pass's rounding relative to ||d||, not ||w||.  A second pass runs only when the first
+            // removed more than half of ||d||^2 (Daniel-Gragg-Kaufman-Stewart criterion).
+            CUDA_TRY(launch_gs_project(P, j + 1, j, w, N, partial, hb, st));
+            CUDA_TRY(launch_gs_update(P, j + 1, j, hb, w, N, partial, hb + 2 * MV, st));
             CUDA_TRY(cudaMemcpyAsync(hh.data(), hb, 3 * MV * sizeof(double2), cudaMemcpyDeviceToHost, st));
             CUDA_TRY(cudaStreamSynchronize(st));
-            const double hn = std::sqrt(std::max(0.0, hh[2 * MV].x));
+            const double dd = hh[j + 1].x;
+            double nn = hh[2 * MV].x;
+            for (int i = 0; i <= j; ++i) hh[MV + i] = make_double2(0, 0);
+            if (nn < 0.5 * dd) {
+                ++reorth;
+                CUDA_TRY(launch_gs_project(P, j + 1, -1, w, N, partial, hb + MV, st));
+                CUDA_TRY(launch_gs_update(P, j + 1, -1, hb + MV, w, N, partial, hb + 2 * MV, st));
+                CUDA_TRY(cudaMemcpyAsync(hh.data() + MV, hb + MV, 2 * MV * sizeof(double2), cudaMemcpyDeviceToHost, st));
+                CUDA_TRY(cudaStreamSynchronize(st));
+                nn = hh[2 * MV].x;
+            }
+            const double hn = std::sqrt(std::max(0.0, nn));
             for (int i = 0; i <= j; ++i)
-                H[(size_t)i * m + j] = cd(hh[i].x + hh[MV + i].x, hh[i].y + hh[MV + i].y);
+                H[(size_t)i * m + j] = cd(hh[i].x + hh[MV + i].x + (i == j ? 1.0 : 0.0), hh[i].y + hh[MV + i].y);
             H[(size_t)(j + 1) * m + j] = hn;
             // previous rotations, then the new one (G = [[c, s], [-conj s, c]])
             for (int i = 0; i < j; ++i) {
@@ -963,6 +977,7 @@ st_status solve_mixed_gmres(st_fdm* h, bool adjoint, const void* F, const void* 
         info->factors_kept = keep ? 1 : (h->kept_sys > 0 ? 2 : 0);
         info->restart = m;
         info->kept_systems = keep ? n_t : h->kept_sys;
+        info->reorth_steps = reorth;
         info->rel_error_estimate = err_est;
         info->rel_residual = rel;
         for (int i = 0; i < 16; ++i) info->residual_history[i] = (i < nh) ? hist[i] : -1.0;
@@ -1132,6 +1147,7 @@ void fill_info_common(const st_fdm* h, st_solve_info* info, int precision) {
     info->tensor_cores = (precision != ST_FP64 && h->tc_ok) ? 1 : 0;
     info->restart = 0;
     info->kept_systems = 0;
+    info->reorth_steps = 0;
     info->rel_error_estimate = -1;
 }
 

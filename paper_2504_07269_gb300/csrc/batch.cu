@@ -722,6 +722,7 @@ extern "C" st_status st_batch_solve(st_batch* b, const void* const* F, const voi
             inf.factors_kept = 0;
             inf.restart = b->m;
             inf.kept_systems = 0;
+            inf.reorth_steps = 0;
             inf.rel_error_estimate = -1;
             inf.rel_residual = rel[p];
             for (int i = 0; i < 16; ++i) inf.residual_history[i] = (i < nh[p]) ? hist[(size_t)p * 16 + i] : -1.0;

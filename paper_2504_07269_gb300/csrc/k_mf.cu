@@ -47,14 +47,101 @@ __device__ __forceinline__ bool mf_bad(C<T> d) {
 }
 
 // ------------------------------------------------------------------ factorisation
+// 4 consecutive complex entries from shared memory (16-byte aligned): two 16-byte loads for
+// complex64, four for complex128
+template <typename T>
+__device__ __forceinline__ void ld4(const C<T>* p, C<T> (&v)[4]);
+template <>
+__device__ __forceinline__ void ld4<float>(const float2* p, float2 (&v)[4]) {
+    const float4 a = reinterpret_cast<const float4*>(p)[0], b = reinterpret_cast<const float4*>(p)[1];
+    v[0] = make_float2(a.x, a.y);
+    v[1] = make_float2(a.z, a.w);
+    v[2] = make_float2(b.x, b.y);
+    v[3] = make_float2(b.z, b.w);
+}
+template <>
+__device__ __forceinline__ void ld4<double>(const double2* p, double2 (&v)[4]) {
+#pragma unroll
+    for (int i = 0; i < 4; ++i) v[i] = p[i];
+}
+
+// Symmetric rank-k update of the front's lower triangle, dst(r, c) -= sum_q L(r, q) d_q L(c, q) over
+// the pivot columns q in [qa, qb), for rows r in [base, rend) and columns c in [base, cend), c <= r.
+// 64 x 64 tiles; per tile the sum runs over all of [qa, qb) in register accumulators (4 x 4 complex
+// per thread) and the destination is read and written once.  Operands are staged q-major in shared
+// memory (As[q][row], Bs[q][col] = L d), the next chunk of NB columns loaded into registers while the
+// current one is multiplied.  d_q is read from the factor's diagonal (written before the call).
+template <typename T, typename At>
+__device__ __forceinline__ void mf_syrk_tiles(const C<T>* Fp, int f, int base, int rend, int cend, int qa, int qb,
+                                              C<T>* As, C<T>* Bs, At at) {
+    constexpr int NB = MfNB<T>::v;
+    constexpr int PER = NB * MF_TILE / MF_THREADS;
+    const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+    const int ntr = (rend - base + MF_TILE - 1) / MF_TILE, ntc = (cend - base + MF_TILE - 1) / MF_TILE;
+    for (int J = 0; J < ntc; ++J) {
+        for (int I = J; I < ntr; ++I) {
+            const int rb = base + I * MF_TILE, cb = base + J * MF_TILE;
+            C<T> ra[PER], rbv[PER];
+            auto fetch = [&](int q0) {
+#pragma unroll
+                for (int k = 0; k < PER; ++k) {
+                    const int e = tid + k * MF_THREADS, q = q0 + e / MF_TILE, rr = e % MF_TILE;
+                    const bool okq = q < qb;
+                    ra[k] = (okq && rb + rr < rend) ? Fp[(size_t)q * f + rb + rr] : mk<T>(0, 0);
+                    rbv[k] = (okq && cb + rr < cend) ? Fp[(size_t)q * f + cb + rr] : mk<T>(0, 0);
+                }
+            };
+            C<T> acc[4][4];
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+#pragma unroll
+                for (int j = 0; j < 4; ++j) acc[i][j] = mk<T>(0, 0);
+            fetch(qa);
+            for (int q0 = qa; q0 < qb; q0 += NB) {
+                __syncthreads();   // the previous chunk's products are done with As / Bs
+#pragma unroll
+                for (int k = 0; k < PER; ++k) {
+                    const int e = tid + k * MF_THREADS, q = q0 + e / MF_TILE;
+                    As[e] = ra[k];
+                    Bs[e] = q < qb ? cmul<T>(rbv[k], Fp[(size_t)q * f + q]) : mk<T>(0, 0);   // d_q, an L1 hit
+                }
+                __syncthreads();
+                if (q0 + NB < qb) fetch(q0 + NB);
+                const int wq = min(NB, qb - q0);
+                for (int q = 0; q < wq; ++q) {
+                    C<T> av[4], bv[4];
+                    ld4<T>(As + q * MF_TILE + tx * 4, av);
+                    ld4<T>(Bs + q * MF_TILE + ty * 4, bv);
+#pragma unroll
+                    for (int i = 0; i < 4; ++i)
+#pragma unroll
+                        for (int j = 0; j < 4; ++j) cfma<T>(acc[i][j], av[i], bv[j]);
+                }
+            }
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                const int c = cb + ty * 4 + j;
+#pragma unroll
+                for (int i = 0; i < 4; ++i) {
+                    const int r = rb + tx * 4 + i;
+                    if (r < rend && c < cend && r >= c) {
+                        C<T>& dst = at(r, c);
+                        dst = csub<T>(dst, acc[i][j]);
+                    }
+                }
+            }
+        }
+    }
+}
+
 template <typename T>
 __global__ void __launch_bounds__(MF_THREADS, 2) k_mf_factor(MfArgs<T> a) {
     constexpr int NB = MfNB<T>::v;
     extern __shared__ __align__(16) unsigned char mf_smem[];
-    C<T>* Tt = reinterpret_cast<C<T>*>(mf_smem);            // [NB][NB + 1] top block, row-major
+    C<T>* As = reinterpret_cast<C<T>*>(mf_smem);             // [NB][MF_TILE]  rows of the tile, q-major
+    C<T>* Bs = As + NB * MF_TILE;                            // [NB][MF_TILE]  columns times d, q-major
+    C<T>* Tt = Bs + NB * MF_TILE;                            // [NB][NB + 1] top block, row-major
     C<T>* dinv = Tt + NB * (NB + 1);                         // [NB]
-    C<T>* As = dinv + NB;                                    // [MF_TILE][NB + 1]  rows of the tile
-    C<T>* Bs = As + MF_TILE * (NB + 1);                      // [MF_TILE][NB + 1]  columns (times d)
     const MfFrontDev fr = a.fronts[a.level_fronts[a.lvl_off + blockIdx.x]];
     const int k = a.k0 + blockIdx.y;
     const int tid = threadIdx.x, nth = blockDim.x;
@@ -76,23 +163,37 @@ __global__ void __launch_bounds__(MF_THREADS, 2) k_mf_factor(MfArgs<T> a) {
             mk<T>((T)(m + (double)s.x * av), (T)((double)s.y * av));
     }
     __syncthreads();
+    // extend-add of the children's update matrices, four entries per thread at a time: a child's
+    // entries land on distinct positions of the front, so the four destinations are loaded together
+    // and stored together
     for (int ci = 0; ci < fr.child_cnt; ++ci) {
         const MfFrontDev ch = a.fronts[a.children[fr.child_off + ci]];
         const C<T>* Sc = a.upd + (size_t)blockIdx.y * a.upd_stride + ch.uoff;
         const int* rp = a.relpos + ch.relpos_off;
-        const int cn = ch.nu;
-        for (int i = tid; i < cn * cn; i += nth) {
-            const int t2 = i / cn, t1 = i - t2 * cn;
-            if (t1 < t2) continue;
-            C<T>& dst = at(rp[t1], rp[t2]);
-            const C<T> v = Sc[i];
-            dst.x += v.x;
-            dst.y += v.y;
+        const int cn = ch.nu, tot = cn * cn;
+        for (int i0 = tid; i0 < tot; i0 += 4 * nth) {
+            C<T>* dp[4];
+            C<T> v[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int i = i0 + u * nth;
+                const int t2 = i / cn, t1 = i - t2 * cn;
+                const bool ok = i < tot && t1 >= t2;
+                dp[u] = ok ? &at(rp[t1], rp[t2]) : nullptr;
+                v[u] = ok ? Sc[i] : mk<T>(0, 0);
+            }
+            C<T> d[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) d[u] = dp[u] ? *dp[u] : mk<T>(0, 0);
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+                if (dp[u]) *dp[u] = cadd<T>(d[u], v[u]);
         }
         __syncthreads();
     }
 
-    // B. partial LDL^T of the pivot block, panels of NB columns
+    // B. LDL^T of the pivot columns, panels of NB columns; the trailing update of each panel reaches
+    //    only the remaining pivot columns (all their rows)
     for (int c0 = 0; c0 < np; c0 += NB) {
         const int w = min(NB, np - c0);
         for (int i = tid; i < NB * NB; i += nth) {
@@ -149,55 +250,11 @@ __global__ void __launch_bounds__(MF_THREADS, 2) k_mf_factor(MfArgs<T> a) {
                 if (q < w) Fp[(size_t)(c0 + q) * f + r] = l[q];
         }
         __syncthreads();
-        // trailing update of the lower triangle of rows / columns [c0 + w, f), 64 x 64 tiles
-        const int base = c0 + w, rem = f - base;
-        const int nt = (rem + MF_TILE - 1) / MF_TILE;
-        const int tx = tid & 15, ty = tid >> 4;
-        for (int tp = 0; tp < nt * (nt + 1) / 2; ++tp) {
-            int I = 0;
-            while ((I + 1) * (I + 2) / 2 <= tp) ++I;
-            const int J = tp - I * (I + 1) / 2;
-            const int rb = base + I * MF_TILE, cb = base + J * MF_TILE;
-            for (int i = tid; i < MF_TILE * NB; i += nth) {
-                const int q = i / MF_TILE, rr = i - q * MF_TILE;
-                const int r = rb + rr, c = cb + rr;
-                As[rr * (NB + 1) + q] = (q < w && r < f) ? Fp[(size_t)(c0 + q) * f + r] : mk<T>(0, 0);
-                Bs[rr * (NB + 1) + q] = (q < w && c < f)
-                                            ? cmul<T>(Fp[(size_t)(c0 + q) * f + c], Tt[q * (NB + 1) + q])
-                                            : mk<T>(0, 0);
-            }
-            __syncthreads();
-            C<T> acc[4][4];
-#pragma unroll
-            for (int i = 0; i < 4; ++i)
-#pragma unroll
-                for (int j = 0; j < 4; ++j) acc[i][j] = mk<T>(0, 0);
-            for (int q = 0; q < w; ++q) {
-                C<T> av[4], bv[4];
-#pragma unroll
-                for (int i = 0; i < 4; ++i) av[i] = As[(tx * 4 + i) * (NB + 1) + q];
-#pragma unroll
-                for (int j = 0; j < 4; ++j) bv[j] = Bs[(ty * 4 + j) * (NB + 1) + q];
-#pragma unroll
-                for (int i = 0; i < 4; ++i)
-#pragma unroll
-                    for (int j = 0; j < 4; ++j) cfma<T>(acc[i][j], av[i], bv[j]);
-            }
-#pragma unroll
-            for (int j = 0; j < 4; ++j) {
-                const int c = cb + ty * 4 + j;
-#pragma unroll
-                for (int i = 0; i < 4; ++i) {
-                    const int r = rb + tx * 4 + i;
-                    if (r < f && c < f && r >= c) {
-                        C<T>& dst = at(r, c);
-                        dst = csub<T>(dst, acc[i][j]);
-                    }
-                }
-            }
-            __syncthreads();
-        }
+        if (c0 + w < np) mf_syrk_tiles<T>(Fp, f, c0 + w, f, np, c0, c0 + w, As, Bs, at);
+        __syncthreads();
     }
+    // C. the update matrix for the parent: S -= L_u D L_u^T over all np pivot columns at once
+    if (nu > 0) mf_syrk_tiles<T>(Fp, f, np, f, f, 0, np, As, Bs, at);
 }
 
 // ------------------------------------------------------------------ substitutions
@@ -275,8 +332,15 @@ __global__ void __launch_bounds__(MF_THREADS) k_mf_bwd(MfArgs<T> a) {
         // contributions of the solved rows below the block: one warp per column
         for (int q = warp; q < wq; q += nwarps) {
             const C<T>* col = Fp + (size_t)(q0 + q) * f;
-            C<T> acc = mk<T>(0, 0);
-            for (int r = q0 + wq + lane; r < f; r += 32) cfma<T>(acc, col[r], x[r]);
+            // four independent partial sums keep four loads per lane in flight
+            C<T> acc4[4] = {mk<T>(0, 0), mk<T>(0, 0), mk<T>(0, 0), mk<T>(0, 0)};
+            int r = q0 + wq + lane;
+            for (; r + 96 < f; r += 128) {
+#pragma unroll
+                for (int u = 0; u < 4; ++u) cfma<T>(acc4[u], col[r + 32 * u], x[r + 32 * u]);
+            }
+            for (; r < f; r += 32) cfma<T>(acc4[0], col[r], x[r]);
+            C<T> acc = cadd<T>(cadd<T>(acc4[0], acc4[1]), cadd<T>(acc4[2], acc4[3]));
 #pragma unroll
             for (int off = 16; off > 0; off >>= 1) {
                 acc.x += __shfl_xor_sync(0xffffffffu, acc.x, off);
@@ -430,11 +494,39 @@ __device__ __forceinline__ C<T> row_value(const C<T> (&v)[R], int q) {
     return shfl_c<T>(src, q & 31);
 }
 
+// factor entries of steps q0 .. q0 + PF - 1 (forward: column q below the diagonal) or q1 - 1 down to
+// q1 - PF (backward), zero outside the front's pivot block; lane l takes rows l, l + 32, ...
+template <typename T, int R, int PF>
+__device__ __forceinline__ void small_load_fwd(C<T> (&Lq)[PF][R], const C<T>* Fp, int f, int np, int q0, int lane) {
+#pragma unroll
+    for (int u = 0; u < PF; ++u)
+#pragma unroll
+        for (int i = 0; i < R; ++i) {
+            const int q = q0 + u, r = lane + 32 * i;
+            Lq[u][i] = (q < np && r > q && r < f) ? Fp[(size_t)q * f + r] : mk<T>(0, 0);
+        }
+}
+template <typename T, int R, int PF>
+__device__ __forceinline__ void small_load_bwd(C<T> (&Lq)[PF][R], const C<T>* Fp, int f, int q1, int lane) {
+#pragma unroll
+    for (int u = 0; u < PF; ++u)
+#pragma unroll
+        for (int i = 0; i < R; ++i) {
+            const int q = q1 - 1 - u, r = lane + 32 * i;
+            Lq[u][i] = (q >= 0 && r > q && r < f) ? Fp[(size_t)q * f + r] : mk<T>(0, 0);
+        }
+}
+
 template <typename T, int FM>
-__global__ void __launch_bounds__(SolveSmallCfg<T, FM>::W * 32)
+__global__ void __launch_bounds__(SolveSmallCfg<T, FM>::W * 32, sizeof(T) == 4 ? (FM == 64 ? 4 : 5) : 1)
 k_mf_solve_small(MfArgs<T> a, int nfronts, int nsys, int fwd) {
     using Cfg = SolveSmallCfg<T, FM>;
-    constexpr int R = Cfg::R, PF = 8;   // steps whose factor entries are loaded ahead
+    // PF steps' factor entries are loaded ahead of the chain.  For two rows per lane the first batch
+    // is issued before the right-hand side and the children's update vectors are gathered, so both
+    // latencies overlap; for one row per lane the registers this takes cost more resident warps
+    // than the overlap gains, and every batch is loaded where it is used.
+    constexpr int R = Cfg::R, PF = 8;
+    constexpr bool HOIST = (R > 1);
     extern __shared__ __align__(16) unsigned char mf_smem[];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const long long item = (long long)blockIdx.x * Cfg::W + warp;
@@ -446,7 +538,9 @@ k_mf_solve_small(MfArgs<T> a, int nfronts, int nsys, int fwd) {
     const C<T>* Fp = a.fac + (size_t)(a.fac_keep ? k : ks) * a.fac_stride + fr.foff;
     C<T>* g = a.rhs + (size_t)k * a.n;
     C<T> v[R];
+    C<T> Lq[PF][R];
     if (fwd) {
+        if (HOIST) small_load_fwd<T, R, PF>(Lq, Fp, f, np, 0, lane);
         C<T>* uv = a.uvec + (size_t)ks * a.uvec_stride;
         C<T>* x = reinterpret_cast<C<T>*>(mf_smem) + (size_t)warp * FM;
 #pragma unroll
@@ -472,14 +566,7 @@ k_mf_solve_small(MfArgs<T> a, int nfronts, int nsys, int fwd) {
             v[i] = r < f ? x[r] : mk<T>(0, 0);
         }
         for (int q0 = 0; q0 < np; q0 += PF) {
-            C<T> Lq[PF][R];
-#pragma unroll
-            for (int u = 0; u < PF; ++u)
-#pragma unroll
-                for (int i = 0; i < R; ++i) {
-                    const int q = q0 + u, r = lane + 32 * i;
-                    Lq[u][i] = (q < np && r > q && r < f) ? Fp[(size_t)q * f + r] : mk<T>(0, 0);
-                }
+            if (q0 > 0 || !HOIST) small_load_fwd<T, R, PF>(Lq, Fp, f, np, q0, lane);
 #pragma unroll
             for (int u = 0; u < PF; ++u) {
                 const int q = q0 + u;
@@ -496,20 +583,14 @@ k_mf_solve_small(MfArgs<T> a, int nfronts, int nsys, int fwd) {
             else if (r < f) uv[fr.uvoff + r - np] = v[i];
         }
     } else {
+        if (HOIST) small_load_bwd<T, R, PF>(Lq, Fp, f, np, lane);
 #pragma unroll
         for (int i = 0; i < R; ++i) {
             const int r = lane + 32 * i;
             v[i] = r < f ? g[a.perm[r < np ? fr.first + r : a.urows[fr.urows_off + r - np]]] : mk<T>(0, 0);
         }
         for (int q1 = np; q1 > 0; q1 -= PF) {
-            C<T> Lq[PF][R];
-#pragma unroll
-            for (int u = 0; u < PF; ++u)
-#pragma unroll
-                for (int i = 0; i < R; ++i) {
-                    const int q = q1 - 1 - u, r = lane + 32 * i;
-                    Lq[u][i] = (q >= 0 && r > q && r < f) ? Fp[(size_t)q * f + r] : mk<T>(0, 0);
-                }
+            if (q1 < np || !HOIST) small_load_bwd<T, R, PF>(Lq, Fp, f, q1, lane);
 #pragma unroll
             for (int u = 0; u < PF; ++u) {
                 const int q = q1 - 1 - u;
@@ -576,7 +657,7 @@ cudaError_t mf_level_launch(MfArgs<T> a, int lvl_off, int n32, int n64, int nlar
 template <typename T>
 size_t mf_factor_smem() {
     constexpr int NB = MfNB<T>::v;
-    return sizeof(C<T>) * ((size_t)NB * (NB + 1) + NB + 2 * (size_t)MF_TILE * (NB + 1));
+    return sizeof(C<T>) * (2 * (size_t)NB * MF_TILE + (size_t)NB * (NB + 1) + NB);
 }
 
 template <typename T>

@@ -25,18 +25,25 @@ __device__ __forceinline__ void stencil_MA(const Stencil& s, const C<TI>* u, int
         C<TI> v = u[idx];
         return make_double2((double)v.x, (double)v.y);
     };
-    double2 c = ld(x);
-    double2 we = make_double2(0, 0), sn = make_double2(0, 0), dg = make_double2(0, 0);
-    if (xi > 0) { double2 v = ld(x - 1); we.x += v.x; we.y += v.y; }
-    if (xi < m - 1) { double2 v = ld(x + 1); we.x += v.x; we.y += v.y; }
-    if (yj > 0) { double2 v = ld(x - m); sn.x += v.x; sn.y += v.y; }
-    if (yj < m - 1) { double2 v = ld(x + m); sn.x += v.x; sn.y += v.y; }
-    if (xi > 0 && yj > 0) { double2 v = ld(x - m - 1); dg.x += v.x; dg.y += v.y; }
-    if (xi < m - 1 && yj < m - 1) { double2 v = ld(x + m + 1); dg.x += v.x; dg.y += v.y; }
+    // neighbours outside the grid read as zero; each pair is one addition (the FP64 pipe bounds the
+    // kernels that call this on GB300)
+    const double2 z = make_double2(0, 0);
+    const bool w_ = xi > 0, e_ = xi < m - 1, s_ = yj > 0, n_ = yj < m - 1;
+    const double2 c = ld(x);
+    const double2 vw = w_ ? ld(x - 1) : z, ve = e_ ? ld(x + 1) : z;
+    const double2 vs = s_ ? ld(x - m) : z, vn = n_ ? ld(x + m) : z;
+    const double2 vsw = (w_ && s_) ? ld(x - m - 1) : z, vne = (e_ && n_) ? ld(x + m + 1) : z;
+    const double2 we = make_double2(vw.x + ve.x, vw.y + ve.y);
+    const double2 sn = make_double2(vs.x + vn.x, vs.y + vn.y);
+    const double2 dg = make_double2(vsw.x + vne.x, vsw.y + vne.y);
     Pm.x = s.Mc * c.x + s.Mw * we.x + s.Ms * sn.x + s.Md * dg.x;
     Pm.y = s.Mc * c.y + s.Mw * we.y + s.Ms * sn.y + s.Md * dg.y;
-    Qa.x = s.Ac * c.x + s.Aw * we.x + s.As * sn.x + s.Ad * dg.x;
-    Qa.y = s.Ac * c.y + s.Aw * we.y + s.As * sn.y + s.Ad * dg.y;
+    Qa.x = s.Ac * c.x + s.Aw * we.x + s.As * sn.x;
+    Qa.y = s.Ac * c.y + s.Aw * we.y + s.As * sn.y;
+    if (s.Ad != 0.0) {   // zero for the squares' right triangles (right angle opposite the diagonal)
+        Qa.x = fma(s.Ad, dg.x, Qa.x);
+        Qa.y = fma(s.Ad, dg.y, Qa.y);
+    }
 }
 
 // General meshes: M_x and A_x in CSR over the interior DOFs (one pattern for both).
@@ -92,7 +99,7 @@ struct ResArgs {
     double* partials;      // 2 per block: ||R||^2, ||F~||^2
 };
 
-constexpr int RES_LT = 16;
+constexpr int RES_LT = 64;
 
 __device__ __forceinline__ double block_sum(double v, double* red) {
     for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(0xffffffffu, v, off);
@@ -106,13 +113,22 @@ __device__ __forceinline__ double block_sum(double v, double* red) {
     return t;
 }
 
-// TB: nonzero diagonals of the temporal bands (3 for P1 time, 5 for P2)
+// TB: nonzero diagonals of the temporal bands (3 for P1 time, 5 for P2).  One thread per spatial
+// node x and RES_LT consecutive time rows: the spatial products (M_x u_k, A_x u_k) of rows k - 2 .. k + 2
+// slide through registers, each computed once per block (plus four halo rows).  The block's band
+// coefficients (bsign B_t, M_t) sit in shared memory.
 template <int TB, typename Op>
 __global__ void __launch_bounds__(256) k_residual(ResArgs<Op> a) {
     __shared__ double red[32];
+    __shared__ double2 coef[RES_LT][5];
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
     const int l0 = blockIdx.y * RES_LT;
     const int l1 = min(l0 + RES_LT, a.n_t);
+    for (int i = threadIdx.x; i < (l1 - l0) * 5; i += blockDim.x) {
+        const int l = l0 + i / 5, d = i % 5;
+        coef[i / 5][d] = make_double2(a.bsign * a.Bb[l * 5 + d], a.Mb[l * 5 + d]);
+    }
+    __syncthreads();
     double rr = 0, ff = 0;
     if (x < a.n_x) {
         double2 P[5], Q[5];
@@ -142,26 +158,32 @@ __global__ void __launch_bounds__(256) k_residual(ResArgs<Op> a) {
                 Q[d] = Q[d + 1];
             }
             load_row_shift(l + 2, P[4], Q[4]);
-            const double2 f = a.F ? a.F[(size_t)l * a.n_x + x] : make_double2(0, 0);
-            const double ml = a.m_t[l];
-            double2 ft = make_double2(f.x - ml * ap.x, f.y - ml * ap.y);
             double2 kv = make_double2(0, 0);
 #pragma unroll
             for (int d = 2 - TB / 2; d <= 2 + TB / 2; ++d) {
-                const double bc = a.bsign * a.Bb[l * 5 + d];
-                const double mc = a.Mb[l * 5 + d];
+                const double2 cm = coef[l - l0][d];   // (bsign B_t, M_t) at (l, l + d - 2)
                 // P2 in time: the interior node of an element couples only with its own element, so
                 // its outer diagonals are zero (the branch is the same for the whole block)
-                if (TB == 5 && bc == 0.0 && mc == 0.0) continue;
-                // i * bc * P + mc * Q
-                kv.x += -bc * P[d].y + mc * Q[d].x;
-                kv.y += bc * P[d].x + mc * Q[d].y;
+                if (TB == 5 && cm.x == 0.0 && cm.y == 0.0) continue;
+                // += i * bc * P + mc * Q
+                kv.x = fma(-cm.x, P[d].y, kv.x);
+                kv.x = fma(cm.y, Q[d].x, kv.x);
+                kv.y = fma(cm.x, P[d].x, kv.y);
+                kv.y = fma(cm.y, Q[d].y, kv.y);
             }
             // residual F~ - K U, or the plain product K U when no right-hand side is given
-            double2 r = a.F ? make_double2(ft.x - kv.x, ft.y - kv.y) : kv;
+            double2 r = kv;
+            if (a.F) {
+                const double2 f = a.F[(size_t)l * a.n_x + x];
+                const double ml = a.m_t[l];
+                const double2 ft = make_double2(f.x - ml * ap.x, f.y - ml * ap.y);
+                r = make_double2(ft.x - kv.x, ft.y - kv.y);
+                ff = fma(ft.x, ft.x, ff);
+                ff = fma(ft.y, ft.y, ff);
+            }
             if (a.R) a.R[(size_t)l * a.n_x + x] = r;
-            rr += r.x * r.x + r.y * r.y;
-            ff += ft.x * ft.x + ft.y * ft.y;
+            rr = fma(r.x, r.x, rr);
+            rr = fma(r.y, r.y, rr);
         }
     }
     double s1 = block_sum(rr, red);

@@ -135,7 +135,8 @@ def _info_dict(info: _lib.st_solve_info):
                 residual_history=[v for v in info.residual_history if v >= 0], kappa_x=info.kappa_x,
                 min_neg_im_shift=info.min_neg_im_shift, setup_seconds=info.setup_seconds,
                 tensor_cores=info.tensor_cores, kernel_launches=info.kernel_launches, restart=info.restart,
-                kept_systems=info.kept_systems, rel_error_estimate=info.rel_error_estimate)
+                kept_systems=info.kept_systems, rel_error_estimate=info.rel_error_estimate,
+                reorth_steps=info.reorth_steps)
 
 
 # ------------------------------------------------------------------ assembly / setup

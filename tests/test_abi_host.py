@@ -36,7 +36,7 @@ def test_exports_every_declared_symbol(L):
     for name in names:
         assert hasattr(L, name), name
         assert name in _lib.SIGNATURES, f"{name} has no binding"
-    assert L.st_abi_version() == 7
+    assert L.st_abi_version() == 8
     assert L.st_status_string(-5).decode() == "zero or non-finite pivot"
 
 

@@ -110,19 +110,24 @@ def test_c4_adjoint_gradient_vs_finite_differences():
     alpha = 1e-3, target and psi0 seeded packets (128x128 squares, P1 time N_t = 256, T = 1).
     The gradient W K^{-H} W e + alpha W f (one adjoint solve) against central differences of J
     (two forward solves each) along 20 seeded complex directions (|d| = |f|).  J is quadratic in f,
-    so the difference quotient has no truncation error for any step; its error is rounding divided
-    by h: that of the forward solves and that of J's own evaluation.  At h = 1e-3 the plain FP64 FDM
-    and plainly summed J values check the gradient to 1e-6.  At the configured h = 1e-6 the forward
-    solves are refined to a 1e-13 FP64 residual and J(f + h d) - J(f - h d) is formed as one sum of
-    differences (the same quantity, without the cancellation of two large sums); the bar is 1e-6 on
-    all 20 directions."""
+    so the difference quotient has no truncation error for any step; its error is the difference of
+    the two forward solves' errors, divided by h, plus J's own rounding.  At h = 1e-3 the plain FP64
+    FDM and plainly summed J values check the gradient to 1e-6.  At the configured h = 1e-6,
+    J(f + h d) - J(f - h d) is formed as one sum of differences (the same quantity, without the
+    cancellation of two large sums), and the forward solves are the mixed-precision refinement run
+    for a fixed number of FP32 applications (the residual target is set out of reach, so the solve
+    stops at max_sweeps): both points then take the same sequence of GMRES steps, and their errors
+    differ by far less than either error.  Printed, not asserted, for comparison: the plain FP64 FDM
+    at h = 1e-6 (its error, about kappa_2(X_t) eps, differs between the two points as rounding does).
+    The bar is 1e-6 on all 20 directions."""
     if not torch.cuda.is_available():
         pytest.skip("no CUDA device")
-    from paper_2504_07269_gb300 import build, stfdm
+    from paper_2504_07269_gb300 import _lib, build, stfdm
 
     build.build()
     dev = torch.device("cuda:0")
     pr = synth.config_problem("c4")
+    FIXED_SWEEPS = 24
     h = stfdm.setup_problem(pr.n, pr.p_t, pr.t_nodes, device=0)
     M_t, B_t, m_t, _ = fe_time.assemble_time(pr.p_t, pr.t_nodes)
     M_x, A_x = fe_space.assemble_space(pr.n)
@@ -139,9 +144,17 @@ def test_c4_adjoint_gradient_vs_finite_differences():
         return np.vdot(a, W(b))
 
     def forward(f, precision="fp64"):
-        # mixed: refined to a 1e-13 FP64 residual, whose rounding (divided by h) stays below the bar
-        psi, _ = stfdm.st_fdm_solve(h, torch.from_numpy(W(f)).to(dev), p0, precision=precision,
-                                    tol=1e-13 if precision == "mixed" else 0.0, max_sweeps=60)
+        if precision == "fp64":                 # the plain FP64 FDM
+            psi, _ = stfdm.st_fdm_solve(h, torch.from_numpy(W(f)).to(dev), p0, precision="fp64")
+            return psi.cpu().numpy()
+        # "fixed": exactly FIXED_SWEEPS FP32 applications of the refinement; the iterate is returned
+        # with ST_ERR_NOT_CONVERGED, since the residual target (1e-30) cannot be met
+        psi = torch.empty((h.n_t, h.n_x), dtype=torch.complex128, device=dev)
+        try:
+            stfdm.st_fdm_solve(h, torch.from_numpy(W(f)).to(dev), p0, psi=psi, precision="mixed", tol=1e-30,
+                               max_sweeps=FIXED_SWEEPS)
+        except _lib.StfdmError as ex:
+            assert ex.status == _lib.ST_ERR_NOT_CONVERGED
         return psi.cpu().numpy()
 
     def J(f, precision="fp64"):
@@ -164,18 +177,21 @@ def test_c4_adjoint_gradient_vs_finite_differences():
         ep, em = forward(fp, precision) - target, forward(fm, precision) - target
         return 0.5 * wdot(ep - em, ep + em).real + 0.5 * alpha * wdot(fp - fm, fp + fm).real
 
-    for hstep, ndir, bar, prec in ((1e-3, 20, 1e-6, "fp64"), (1e-6, 20, 1e-6, "mixed")):
+    for hstep, bar, prec, diff in ((1e-3, 1e-6, "fp64", False), (1e-6, None, "fp64", True),
+                                   (1e-6, 1e-6, "fixed", True)):
         gaps = []
-        for d in dirs[:ndir]:
-            if prec == "fp64":
-                fd = (J(f + hstep * d, prec) - J(f - hstep * d, prec)) / (2 * hstep)
-            else:
+        for d in dirs:
+            if diff:
                 fd = J_diff(f + hstep * d, f - hstep * d, prec) / (2 * hstep)
+            else:
+                fd = (J(f + hstep * d, prec) - J(f - hstep * d, prec)) / (2 * hstep)
             ad = np.vdot(g, d).real
             gaps.append(abs(fd - ad) / abs(ad))
-        print(f"c4 adjoint gradient vs central differences, h = {hstep:g} ({ndir} directions, forward solves "
-              f"{prec}): relative gaps max {max(gaps):.2e}, median {np.median(gaps):.2e}")
-        assert max(gaps) <= bar
+        print(f"c4 adjoint gradient vs central differences, h = {hstep:g} ({len(dirs)} directions, forward solves "
+              f"{prec}{', J as one sum of differences' if diff else ''}): relative gaps max {max(gaps):.2e}, "
+              f"median {np.median(gaps):.2e}{'' if bar else ' (printed only)'}")
+        if bar is not None:
+            assert max(gaps) <= bar
     # the mixed-precision adjoint (FP32 FDM refined by FP64 GMRES) against the FP64 adjoint
     try:
         lam32, info = stfdm.st_adjoint_solve(h, torch.from_numpy(W(e)).to(dev), precision="mixed", tol=1e-11,
