@@ -163,30 +163,39 @@ __global__ void __launch_bounds__(MF_THREADS, 2) k_mf_factor(MfArgs<T> a) {
             mk<T>((T)(m + (double)s.x * av), (T)((double)s.y * av));
     }
     __syncthreads();
-    // extend-add of the children's update matrices, four entries per thread at a time: a child's
-    // entries land on distinct positions of the front, so the four destinations are loaded together
-    // and stored together
+    // extend-add of the children's update matrices.  The child's relative positions are staged in
+    // shared memory (in the operand tiles, unused until the panels), and each thread handles eight
+    // entries at a time: a child's entries land on distinct positions of the front, so the eight
+    // destinations are loaded together and stored together.
+    constexpr int EA = 8;
+    int* rps = reinterpret_cast<int*>(As);
+    constexpr int RPS_CAP = (int)(2 * NB * MF_TILE * sizeof(C<T>) / sizeof(int));
     for (int ci = 0; ci < fr.child_cnt; ++ci) {
         const MfFrontDev ch = a.fronts[a.children[fr.child_off + ci]];
         const C<T>* Sc = a.upd + (size_t)blockIdx.y * a.upd_stride + ch.uoff;
-        const int* rp = a.relpos + ch.relpos_off;
         const int cn = ch.nu, tot = cn * cn;
-        for (int i0 = tid; i0 < tot; i0 += 4 * nth) {
-            C<T>* dp[4];
-            C<T> v[4];
+        const int* rp = a.relpos + ch.relpos_off;
+        if (cn <= RPS_CAP) {
+            for (int t = tid; t < cn; t += nth) rps[t] = rp[t];
+            __syncthreads();
+            rp = rps;
+        }
+        for (int i0 = tid; i0 < tot; i0 += EA * nth) {
+            C<T>* dp[EA];
+            C<T> v[EA];
 #pragma unroll
-            for (int u = 0; u < 4; ++u) {
+            for (int u = 0; u < EA; ++u) {
                 const int i = i0 + u * nth;
                 const int t2 = i / cn, t1 = i - t2 * cn;
                 const bool ok = i < tot && t1 >= t2;
                 dp[u] = ok ? &at(rp[t1], rp[t2]) : nullptr;
                 v[u] = ok ? Sc[i] : mk<T>(0, 0);
             }
-            C<T> d[4];
+            C<T> d[EA];
 #pragma unroll
-            for (int u = 0; u < 4; ++u) d[u] = dp[u] ? *dp[u] : mk<T>(0, 0);
+            for (int u = 0; u < EA; ++u) d[u] = dp[u] ? *dp[u] : mk<T>(0, 0);
 #pragma unroll
-            for (int u = 0; u < 4; ++u)
+            for (int u = 0; u < EA; ++u)
                 if (dp[u]) *dp[u] = cadd<T>(d[u], v[u]);
         }
         __syncthreads();
@@ -380,8 +389,11 @@ struct SmallCfg {
 };
 __device__ __forceinline__ int tri_row(int r) { return (r * (r + 1)) >> 1; }
 
+// resident CTAs per SM that the shared-memory tiles allow (complex64 fronts of <= 32 rows: six);
+// the register budget is held to it
 template <typename T, int FM>
-__global__ void __launch_bounds__(SmallCfg<T, FM>::W * 32) k_mf_factor_small(MfArgs<T> a, int nfronts, int nsys) {
+__global__ void __launch_bounds__(SmallCfg<T, FM>::W * 32, (sizeof(T) == 4 && FM == 32) ? 6 : 2)
+k_mf_factor_small(MfArgs<T> a, int nfronts, int nsys) {
     using Cfg = SmallCfg<T, FM>;
     constexpr int R = Cfg::R;
     extern __shared__ __align__(16) unsigned char mf_smem[];
@@ -410,18 +422,33 @@ __global__ void __launch_bounds__(SmallCfg<T, FM>::W * 32) k_mf_factor_small(MfA
             mk<T>((T)(m + (double)s.x * av), (T)((double)s.y * av));
     }
     __syncwarp();
+    // extend-add: each lane loads EB of the child's entries (and their positions) before adding them
+    // into the shared-memory front (EB = 4 for fronts of <= 32 rows keeps their registers within the
+    // six resident CTAs the tiles allow)
+    constexpr int EB = (R == 1) ? 4 : 8;
     for (int ci = 0; ci < fr.child_cnt; ++ci) {
         const MfFrontDev ch = a.fronts[a.children[fr.child_off + ci]];
         const C<T>* Sc = a.upd + (size_t)ks * a.upd_stride + ch.uoff;
         const int* rp = a.relpos + ch.relpos_off;
-        const int cn = ch.nu;
-        for (int i = lane; i < cn * cn; i += 32) {
-            const int t2 = i / cn, t1 = i - t2 * cn;
-            if (t1 < t2) continue;
-            C<T>& dst = F[tri_row(rp[t1]) + rp[t2]];
-            const C<T> v = Sc[i];
-            dst.x += v.x;
-            dst.y += v.y;
+        const int cn = ch.nu, tot = cn * cn;
+        for (int i0 = lane; i0 < tot; i0 += EB * 32) {
+            int pos[EB];
+            C<T> v[EB];
+#pragma unroll
+            for (int u = 0; u < EB; ++u) {
+                const int i = i0 + 32 * u;
+                const int t2 = i / cn, t1 = i - t2 * cn;
+                const bool ok = i < tot && t1 >= t2;
+                pos[u] = ok ? tri_row(rp[t1]) + rp[t2] : -1;
+                v[u] = ok ? Sc[i] : mk<T>(0, 0);
+            }
+#pragma unroll
+            for (int u = 0; u < EB; ++u)
+                if (pos[u] >= 0) {
+                    C<T>& dst = F[pos[u]];
+                    dst.x += v[u].x;
+                    dst.y += v[u].y;
+                }
         }
         __syncwarp();
     }
