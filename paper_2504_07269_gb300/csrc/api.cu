@@ -407,8 +407,10 @@ cudaError_t mf_levels(const st_fdm* h, MfArgs<T>& a, int k0, int cnt, int what, 
     for (int i = 0; i < H; ++i) {
         const int l = (what == 2) ? H - 1 - i : i;   // backward substitution from the root
         const int n = P.level_ptr[l + 1] - P.level_ptr[l];
-        const int n32 = P.level_n32[l], n64 = P.level_n64[l];
-        cudaError_t e = mf_level_launch<T>(a, P.level_ptr[l], n32, n64, n - n32 - n64, cnt, P.max_front, what, st);
+        const int* ncls = P.level_ncls.data() + (size_t)l * MF_NCLS;
+        int nsmall = 0;
+        for (int c = 0; c < MF_NCLS; ++c) nsmall += ncls[c];
+        cudaError_t e = mf_level_launch<T>(a, P.level_ptr[l], ncls, n - nsmall, cnt, P.max_front, what, st);
         if (e != cudaSuccess) return e;
     }
     return cudaSuccess;

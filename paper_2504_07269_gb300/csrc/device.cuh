@@ -210,7 +210,7 @@ template <typename T> cudaError_t mf_factor_launch(MfArgs<T> a, int lvl_off, int
 template <typename T>
 cudaError_t mf_solve_launch(MfArgs<T> a, int lvl_off, int nfronts, int nsys, int max_front, bool fwd, cudaStream_t st);
 template <typename T>
-cudaError_t mf_level_launch(MfArgs<T> a, int lvl_off, int n32, int n64, int nlarge, int nsys, int max_front, int what,
+cudaError_t mf_level_launch(MfArgs<T> a, int lvl_off, const int* ncls, int nlarge, int nsys, int max_front, int what,
                             cudaStream_t st);
 
 // CSR spatial operators on the device (general meshes)

@@ -220,20 +220,18 @@ st_status build_mf_plan(const MeshSpace& ms, int leaf, MfPlan& P) {
     P.level_fronts.assign(F, 0);
     std::vector<int> fill(P.level_ptr.begin(), P.level_ptr.end() - 1);
     for (int f = 0; f < F; ++f) P.level_fronts[fill[P.fronts[f].height]++] = f;
-    // within a level: the fronts that one warp handles (f <= 32, then f <= 64) before the large ones
-    P.level_n32.assign(maxh + 1, 0);
-    P.level_n64.assign(maxh + 1, 0);
+    // within a level: the fronts that one warp handles (f <= 32, 64, 96, 128) before the large ones
+    P.level_ncls.assign((size_t)(maxh + 1) * MF_NCLS, 0);
     for (int h = 0; h <= maxh; ++h) {
         auto cls = [&](int fi) {
             const int fs = P.fronts[fi].np + P.fronts[fi].nu;
-            return fs <= 32 ? 0 : fs <= 64 ? 1 : 2;
+            return fs <= 32 * MF_NCLS ? (fs - 1) / 32 : MF_NCLS;
         };
         std::stable_sort(P.level_fronts.begin() + P.level_ptr[h], P.level_fronts.begin() + P.level_ptr[h + 1],
                          [&](int x, int y) { return cls(x) < cls(y); });
         for (int i = P.level_ptr[h]; i < P.level_ptr[h + 1]; ++i) {
             const int c = cls(P.level_fronts[i]);
-            if (c == 0) P.level_n32[h] += 1;
-            else if (c == 1) P.level_n64[h] += 1;
+            if (c < MF_NCLS) P.level_ncls[(size_t)h * MF_NCLS + c] += 1;
         }
     }
     // Update matrices live from their front's level until their parent's level has assembled them.

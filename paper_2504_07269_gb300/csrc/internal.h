@@ -74,15 +74,17 @@ struct MfFront {
     int child_off = 0, child_cnt = 0; // children[child_off .. + child_cnt)
 };
 
+constexpr int MF_NCLS = 4;                      // warp-per-front size classes: f <= 32, 64, 96, 128
 struct MfPlan {
     int n = 0;
     std::vector<int> perm, iperm;      // new -> old, old -> new
     std::vector<MfFront> fronts;
     std::vector<int> urows, relpos, children;
     std::vector<int> orig_r, orig_c, orig_k;
-    std::vector<int> level_ptr, level_fronts;   // fronts by height (leaves first); within a level the
-                                                // fronts with f <= 32, then f <= 64, then the rest
-    std::vector<int> level_n32, level_n64;      // per level: fronts with f <= 32, with 32 < f <= 64
+    std::vector<int> level_ptr, level_fronts;   // fronts by height (leaves first); within a level by
+                                                // size class: f <= 32, <= 64, <= 96, <= 128, then the rest
+    std::vector<int> level_ncls;                // per level, MF_NCLS counts: fronts of each size class
+                                                // that one warp factorises and solves
     long long factor_entries = 0, update_entries = 0, uvec_entries = 0;
     int max_front = 0, max_np = 0;
     double flops_cmac = 0;             // complex multiply-adds of one factorisation

@@ -69,8 +69,10 @@ __device__ __forceinline__ void ld4<double>(const double2* p, double2 (&v)[4]) {
 // the pivot columns q in [qa, qb), for rows r in [base, rend) and columns c in [base, cend), c <= r.
 // 64 x 64 tiles; per tile the sum runs over all of [qa, qb) in register accumulators (4 x 4 complex
 // per thread) and the destination is read and written once.  Operands are staged q-major in shared
-// memory (As[q][row], Bs[q][col] = L d), the next chunk of NB columns loaded into registers while the
-// current one is multiplied.  d_q is read from the factor's diagonal (written before the call).
+// memory (As[q][row], Bs[q][col] = L d) by chunks of NB columns.  The (tile, chunk) steps form one
+// sequence, and the next step's operands (the next chunk, or the next tile's first chunk) are loaded
+// into registers while the current one is multiplied, so a tile's loads overlap the previous tile's
+// products and write-back.  d_q is read from the factor's diagonal (written before the call).
 template <typename T, typename At>
 __device__ __forceinline__ void mf_syrk_tiles(const C<T>* Fp, int f, int base, int rend, int cend, int qa, int qb,
                                               C<T>* As, C<T>* Bs, At at) {
@@ -78,59 +80,86 @@ __device__ __forceinline__ void mf_syrk_tiles(const C<T>* Fp, int f, int base, i
     constexpr int PER = NB * MF_TILE / MF_THREADS;
     const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
     const int ntr = (rend - base + MF_TILE - 1) / MF_TILE, ntc = (cend - base + MF_TILE - 1) / MF_TILE;
-    for (int J = 0; J < ntc; ++J) {
-        for (int I = J; I < ntr; ++I) {
-            const int rb = base + I * MF_TILE, cb = base + J * MF_TILE;
-            C<T> ra[PER], rbv[PER];
-            auto fetch = [&](int q0) {
+    const int nch = (qb - qa + NB - 1) / NB;
+    if (ntc <= 0 || ntr <= 0 || nch <= 0) return;
+    C<T> ra[PER], rbv[PER];
+    auto fetch = [&](int I, int J, int c) {
+        const int rb = base + I * MF_TILE, cb = base + J * MF_TILE, q0 = qa + c * NB;
 #pragma unroll
-                for (int k = 0; k < PER; ++k) {
-                    const int e = tid + k * MF_THREADS, q = q0 + e / MF_TILE, rr = e % MF_TILE;
-                    const bool okq = q < qb;
-                    ra[k] = (okq && rb + rr < rend) ? Fp[(size_t)q * f + rb + rr] : mk<T>(0, 0);
-                    rbv[k] = (okq && cb + rr < cend) ? Fp[(size_t)q * f + cb + rr] : mk<T>(0, 0);
-                }
-            };
-            C<T> acc[4][4];
+        for (int k = 0; k < PER; ++k) {
+            const int e = tid + k * MF_THREADS, q = q0 + e / MF_TILE, rr = e % MF_TILE;
+            const bool okq = q < qb;
+            ra[k] = (okq && rb + rr < rend) ? Fp[(size_t)q * f + rb + rr] : mk<T>(0, 0);
+            rbv[k] = (okq && cb + rr < cend) ? Fp[(size_t)q * f + cb + rr] : mk<T>(0, 0);
+        }
+    };
+    C<T> acc[4][4];
 #pragma unroll
-            for (int i = 0; i < 4; ++i)
+    for (int i = 0; i < 4; ++i)
 #pragma unroll
-                for (int j = 0; j < 4; ++j) acc[i][j] = mk<T>(0, 0);
-            fetch(qa);
-            for (int q0 = qa; q0 < qb; q0 += NB) {
-                __syncthreads();   // the previous chunk's products are done with As / Bs
+        for (int j = 0; j < 4; ++j) acc[i][j] = mk<T>(0, 0);
+    int I = 0, J = 0, c = 0;   // the current step: tile (I, J), I >= J, column chunk c
+    fetch(0, 0, 0);
+    while (true) {
+        const int q0 = qa + c * NB;
+        __syncthreads();   // the previous step's products are done with As / Bs
 #pragma unroll
-                for (int k = 0; k < PER; ++k) {
-                    const int e = tid + k * MF_THREADS, q = q0 + e / MF_TILE;
-                    As[e] = ra[k];
-                    Bs[e] = q < qb ? cmul<T>(rbv[k], Fp[(size_t)q * f + q]) : mk<T>(0, 0);   // d_q, an L1 hit
-                }
-                __syncthreads();
-                if (q0 + NB < qb) fetch(q0 + NB);
-                const int wq = min(NB, qb - q0);
-                for (int q = 0; q < wq; ++q) {
-                    C<T> av[4], bv[4];
-                    ld4<T>(As + q * MF_TILE + tx * 4, av);
-                    ld4<T>(Bs + q * MF_TILE + ty * 4, bv);
+        for (int k = 0; k < PER; ++k) {
+            const int e = tid + k * MF_THREADS, q = q0 + e / MF_TILE;
+            As[e] = ra[k];
+            Bs[e] = q < qb ? cmul<T>(rbv[k], Fp[(size_t)q * f + q]) : mk<T>(0, 0);   // d_q, an L1 hit
+        }
+        __syncthreads();
+        int nI = I, nJ = J, nc = c + 1;
+        if (nc == nch) {
+            nc = 0;
+            if (++nI == ntr) nI = ++nJ;
+        }
+        const bool more = nJ < ntc;
+        if (more) fetch(nI, nJ, nc);
+        const int wq = min(NB, qb - q0);
+        if (wq == NB) {
+#pragma unroll 4
+            for (int q = 0; q < NB; ++q) {
+                C<T> av[4], bv[4];
+                ld4<T>(As + q * MF_TILE + tx * 4, av);
+                ld4<T>(Bs + q * MF_TILE + ty * 4, bv);
 #pragma unroll
-                    for (int i = 0; i < 4; ++i)
+                for (int i = 0; i < 4; ++i)
 #pragma unroll
-                        for (int j = 0; j < 4; ++j) cfma<T>(acc[i][j], av[i], bv[j]);
-                }
+                    for (int j = 0; j < 4; ++j) cfma<T>(acc[i][j], av[i], bv[j]);
             }
+        } else {
+            for (int q = 0; q < wq; ++q) {
+                C<T> av[4], bv[4];
+                ld4<T>(As + q * MF_TILE + tx * 4, av);
+                ld4<T>(Bs + q * MF_TILE + ty * 4, bv);
+#pragma unroll
+                for (int i = 0; i < 4; ++i)
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) cfma<T>(acc[i][j], av[i], bv[j]);
+            }
+        }
+        if (c == nch - 1) {   // the tile's sum is complete: subtract it from the destination
+            const int rb = base + I * MF_TILE, cb = base + J * MF_TILE;
 #pragma unroll
             for (int j = 0; j < 4; ++j) {
-                const int c = cb + ty * 4 + j;
+                const int cc = cb + ty * 4 + j;
 #pragma unroll
                 for (int i = 0; i < 4; ++i) {
                     const int r = rb + tx * 4 + i;
-                    if (r < rend && c < cend && r >= c) {
-                        C<T>& dst = at(r, c);
+                    if (r < rend && cc < cend && r >= cc) {
+                        C<T>& dst = at(r, cc);
                         dst = csub<T>(dst, acc[i][j]);
                     }
+                    acc[i][j] = mk<T>(0, 0);
                 }
             }
         }
+        if (!more) break;
+        I = nI;
+        J = nJ;
+        c = nc;
     }
 }
 
@@ -500,7 +529,8 @@ k_mf_factor_small(MfArgs<T> a, int nfronts, int nsys) {
         }
 }
 
-// Substitutions for fronts with f <= FM: one warp per (front, system), the front vector in registers
+// Substitutions for fronts with f <= FM (32, 64, 96 or 128): one warp per (front, system), the front
+// vector in registers
 // (lane l holds rows l, l + 32, ...), the pivot value of each step broadcast by a shuffle from its
 // owner, the factor entries read straight from global memory (column q of the block is contiguous,
 // so a step's loads are coalesced; they do not depend on the chain and are issued ahead of it).
@@ -545,7 +575,7 @@ __device__ __forceinline__ void small_load_bwd(C<T> (&Lq)[PF][R], const C<T>* Fp
 }
 
 template <typename T, int FM>
-__global__ void __launch_bounds__(SolveSmallCfg<T, FM>::W * 32, sizeof(T) == 4 ? (FM == 64 ? 4 : 5) : 1)
+__global__ void __launch_bounds__(SolveSmallCfg<T, FM>::W * 32, sizeof(T) == 4 ? (FM == 32 ? 5 : (FM == 64 ? 4 : 2)) : 1)
 k_mf_solve_small(MfArgs<T> a, int nfronts, int nsys, int fwd) {
     using Cfg = SolveSmallCfg<T, FM>;
     // PF steps' factor entries are loaded ahead of the chain.  For two rows per lane the first batch
@@ -655,9 +685,14 @@ cudaError_t mf_small_launch(MfArgs<T> a, int lvl_off, int nfronts, int nsys, int
     if (blocks > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
     cudaError_t e;
     if (what == 0) {
-        e = cudaFuncSetAttribute(k_mf_factor_small<T, FM>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Cfg::SMEM);
-        if (e != cudaSuccess) return e;
-        k_mf_factor_small<T, FM><<<(unsigned)blocks, Cfg::W * 32, Cfg::SMEM, st>>>(a, nfronts, nsys);
+        if constexpr (FM <= 64) {   // larger fronts are factorised by the CTA kernel
+            e = cudaFuncSetAttribute(k_mf_factor_small<T, FM>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)Cfg::SMEM);
+            if (e != cudaSuccess) return e;
+            k_mf_factor_small<T, FM><<<(unsigned)blocks, Cfg::W * 32, Cfg::SMEM, st>>>(a, nfronts, nsys);
+        } else {
+            return cudaErrorInvalidValue;
+        }
     } else {
         using SCfg = SolveSmallCfg<T, FM>;
         const long long sblocks = (items + SCfg::W - 1) / SCfg::W;
@@ -668,16 +703,31 @@ cudaError_t mf_small_launch(MfArgs<T> a, int lvl_off, int nfronts, int nsys, int
     return cudaGetLastError();
 }
 
-// one launch level: fronts [lvl_off, lvl_off + n32) have f <= 32, the next n64 have f <= 64, the rest
-// are large; what: 0 factorise, 1 forward, 2 backward
+// one launch level: the first ncls[0] fronts from lvl_off have f <= 32, the next ncls[1] f <= 64,
+// ncls[2] f <= 96, ncls[3] f <= 128, the remaining nlarge are large; what: 0 factorise, 1 forward,
+// 2 backward.  Substitutions run one warp per front up to f = 128.  Factorisations run one warp per
+// front only up to f = 64: from f = 65 on, the CTA kernel's tiled updates beat one warp's
+// sequential pivot loop over the larger shared-memory tile (measured on the 384^2 grid: 216 ms by
+// warps for the fronts of 65 to 128 rows against about 90 ms by CTAs).
 template <typename T>
-cudaError_t mf_level_launch(MfArgs<T> a, int lvl_off, int n32, int n64, int nlarge, int nsys, int max_front, int what,
+cudaError_t mf_level_launch(MfArgs<T> a, int lvl_off, const int* ncls, int nlarge, int nsys, int max_front, int what,
                             cudaStream_t st) {
-    cudaError_t e = mf_small_launch<T, 32>(a, lvl_off, n32, nsys, what, st);
-    if (e == cudaSuccess) e = mf_small_launch<T, 64>(a, lvl_off + n32, n64, nsys, what, st);
+    int off = lvl_off;
+    cudaError_t e = mf_small_launch<T, 32>(a, off, ncls[0], nsys, what, st);
+    off += ncls[0];
+    if (e == cudaSuccess) e = mf_small_launch<T, 64>(a, off, ncls[1], nsys, what, st);
+    off += ncls[1];
+    if (e != cudaSuccess) return e;
+    if (what == 0) {
+        const int n = ncls[2] + ncls[3] + nlarge;
+        return n > 0 ? mf_factor_launch<T>(a, off, n, nsys, st) : cudaSuccess;
+    }
+    e = mf_small_launch<T, 96>(a, off, ncls[2], nsys, what, st);
+    off += ncls[2];
+    if (e == cudaSuccess) e = mf_small_launch<T, 128>(a, off, ncls[3], nsys, what, st);
+    off += ncls[3];
     if (e != cudaSuccess || nlarge <= 0) return e;
-    if (what == 0) return mf_factor_launch<T>(a, lvl_off + n32 + n64, nlarge, nsys, st);
-    return mf_solve_launch<T>(a, lvl_off + n32 + n64, nlarge, nsys, max_front, what == 1, st);
+    return mf_solve_launch<T>(a, off, nlarge, nsys, max_front, what == 1, st);
 }
 
 // ------------------------------------------------------------------ launchers
@@ -721,8 +771,8 @@ cudaError_t mf_solve_launch(MfArgs<T> a, int lvl_off, int nfronts, int nsys, int
     return cudaGetLastError();
 }
 
-template cudaError_t mf_level_launch<float>(MfArgs<float>, int, int, int, int, int, int, int, cudaStream_t);
-template cudaError_t mf_level_launch<double>(MfArgs<double>, int, int, int, int, int, int, int, cudaStream_t);
+template cudaError_t mf_level_launch<float>(MfArgs<float>, int, const int*, int, int, int, int, cudaStream_t);
+template cudaError_t mf_level_launch<double>(MfArgs<double>, int, const int*, int, int, int, int, cudaStream_t);
 template cudaError_t mf_factor_launch<float>(MfArgs<float>, int, int, int, cudaStream_t);
 template cudaError_t mf_factor_launch<double>(MfArgs<double>, int, int, int, cudaStream_t);
 template cudaError_t mf_solve_launch<float>(MfArgs<float>, int, int, int, int, bool, cudaStream_t);

@@ -174,7 +174,7 @@ def test_c4_adjoint_gradient_vs_finite_differences():
         # a^H W a - b^H W b = Re (a - b)^H W (a + b) for Hermitian W.  J itself is dominated by terms
         # that do not change along d, so subtracting two summed J values loses about |J| eps sqrt(n)
         # to rounding, which 1/h amplifies far beyond the bar at h = 1e-6.
-        if precision == "warm":
+        if precision == "pair":
             pp, pm = forward_pair(fp, fm)
         else:
             pp, pm = forward(fp, precision), forward(fm, precision)
@@ -182,7 +182,7 @@ def test_c4_adjoint_gradient_vs_finite_differences():
         return 0.5 * wdot(ep - em, ep + em).real + 0.5 * alpha * wdot(fp - fm, fp + fm).real
 
     for hstep, bar, prec, diff in ((1e-3, 1e-6, "fp64", False), (1e-6, None, "fp64", True),
-                                   (1e-6, 1e-6, "warm", True)):
+                                   (1e-6, 1e-6, "pair", True)):
         gaps = []
         for d in dirs:
             if diff:
@@ -191,8 +191,9 @@ def test_c4_adjoint_gradient_vs_finite_differences():
                 fd = (J(f + hstep * d, prec) - J(f - hstep * d, prec)) / (2 * hstep)
             ad = np.vdot(g, d).real
             gaps.append(abs(fd - ad) / abs(ad))
+        how = "mixed, the second from the load difference" if prec == "pair" else prec
         print(f"c4 adjoint gradient vs central differences, h = {hstep:g} ({len(dirs)} directions, forward solves "
-              f"{prec}{', J as one sum of differences' if diff else ''}): relative gaps max {max(gaps):.2e}, "
+              f"{how}{', J as one sum of differences' if diff else ''}): relative gaps max {max(gaps):.2e}, "
               f"median {np.median(gaps):.2e}{'' if bar else ' (printed only)'}")
         if bar is not None:
             assert max(gaps) <= bar
