@@ -222,6 +222,7 @@ cudaError_t launch_multiaxpy(const double2* const* Vdev, int nv, const double2* 
 cudaError_t launch_gs_project(const double2* const* Vdev, int nv, int shift, const double2* w, size_t n,
                               double2* partial, double2* out, cudaStream_t st) {
     if (nv < 1 || nv + 1 > KRY_MAXV || shift >= nv) return cudaErrorInvalidValue;
+    if ((size_t)GS_BLOCKS * (nv + 1) > (size_t)KRY_BLOCKS * KRY_MAXV) return cudaErrorInvalidValue;   // partials
     dim3 grid(GS_BLOCKS, (nv + GS_CHUNK - 1) / GS_CHUNK);
     k_gs_project<<<grid, 256, 0, st>>>(Vdev, nv, shift, w, n, partial);
     cudaError_t e = cudaGetLastError();
