@@ -99,9 +99,10 @@ __global__ void __launch_bounds__(256) k_multiaxpy(const double2* const* V, int 
 // One Gram-Schmidt pass of the Arnoldi step on d = w - V_s (s = shift >= 0; d = w when shift < 0).
 // Project: partial[b * (nv + 1) + i] = this block's part of conj(V_i)^T d for i < nv, and of ||d||^2 in
 // slot nv; blockIdx.y selects a chunk of GS_CHUNK vectors (w and V_s are read once per chunk, the
-// norm is summed by chunk 0 only).
-constexpr int GS_CHUNK = 8;
-constexpr int GS_BLOCKS = 456;   // 3 x 152 SMs: k_gs_project's 80 registers allow three 256-thread blocks per SM
+// norm is summed by chunk 0 only).  Chunks of 4 with five blocks per SM ran faster than chunks of 8
+// (three blocks per SM) or 16 (two): 79 / 107 / 206 ms per 384^2/P2-1024 solve.
+constexpr int GS_CHUNK = 4;
+constexpr int GS_BLOCKS = 760;   // 5 x 152 SMs: k_gs_project (48 registers) keeps five 256-thread blocks per SM
 __global__ void __launch_bounds__(256) k_gs_project(const double2* const* V, int nv, int shift, const double2* w,
                                                     size_t n, double2* partial) {
     __shared__ double2 red[8][GS_CHUNK + 1];
