@@ -577,7 +577,7 @@ def multifrontal_rooflines(stfdm, h, pr, kprec, dev, clocks, config):
     nbytes = pr.n_t * (2.0 * plan["factor_entries"] * esz + 6.0 * pr.n_x * esz)
     peaks = measured_peaks() or {}
     hbm = peaks.get("hbm_gbs", 6800.0)
-    sub = {"bound": "hbm", "kernel": "k_mf_solve_small<32|64> + k_mf_fwd + k_mf_bwd (every level, both directions)",
+    sub = {"bound": "hbm", "kernel": "k_mf_solve_small<32|64|96|128> + k_mf_fwd + k_mf_bwd (every level, both directions)",
            "achieved": nbytes / ts / 1e9, "peak": hbm, "unit": "GB/s", "frac": nbytes / ts / 1e9 / hbm,
            "traffic": profiled_traffic(f"mf_subst_{kprec}_{config}", "mf"), "launch_ms": ts * 1e3,
            "algorithmic_bytes": nbytes,

@@ -10,6 +10,7 @@ free memory; and that a size beyond the fixed array is refused.  The file is nam
 every other test file.
 """
 import ctypes
+import gc
 
 import numpy as np
 import pytest
@@ -78,15 +79,23 @@ def test_residual_noalloc_allocates_nothing():
     got = [(torch.empty_like(F), torch.empty_like(norms)) for _ in psis]   # allocated before measuring
     stfdm.st_residual_noalloc(h, F, psi0, psis[0], R, norms)     # warm-up
     torch.cuda.synchronize()
-    alloc0 = torch.cuda.memory_allocated(dev)
-    free0, _ = torch.cuda.mem_get_info(dev)
-    for psi, (Rg, ng) in zip(psis, got):
-        stfdm.st_residual_noalloc(h, F, psi0, psi, R, norms)
-        Rg.copy_(R)
-        ng.copy_(norms)
-    torch.cuda.synchronize()
-    free1, _ = torch.cuda.mem_get_info(dev)
-    assert torch.cuda.memory_allocated(dev) == alloc0
+    # tensors left for the garbage collector by earlier tests in this process would otherwise be
+    # freed at a random point of the measured calls and change torch's count
+    gc.collect()
+    gc.disable()
+    try:
+        alloc0 = torch.cuda.memory_allocated(dev)
+        free0, _ = torch.cuda.mem_get_info(dev)
+        for psi, (Rg, ng) in zip(psis, got):
+            stfdm.st_residual_noalloc(h, F, psi0, psi, R, norms)
+            Rg.copy_(R)
+            ng.copy_(norms)
+        torch.cuda.synchronize()
+        free1, _ = torch.cuda.mem_get_info(dev)
+        alloc1 = torch.cuda.memory_allocated(dev)
+    finally:
+        gc.enable()
+    assert alloc1 == alloc0
     assert free1 == free0
     for psi, (Rg, ng) in zip(psis, got):
         rel_ref, _ = stfdm.st_residual(h, F, psi0, psi, R_ref)
