@@ -5,15 +5,19 @@
 // ordering and assembly tree come from the host plan (nested dissection, host_mf.cpp); every C_k
 // has the same sparsity, so the device work is batched over k.
 //
-// One CTA per (front, system k) and launch level (fronts of equal height in the assembly tree):
+// Launch levels are fronts of equal height in the assembly tree.  Fronts of up to 64 rows are
+// factorised by one warp each (the whole lower triangle in shared memory), fronts of up to 128 rows
+// are solved by one warp each (the front vector in registers); the larger ones take one CTA per
+// (front, system k):
 //   factor  the front (np pivots, nu update rows, f = np + nu) is assembled from the entries of
 //           M_x + s_k A_x in its pivot columns and the children's update matrices (extend-add),
-//           then its pivot block is factorised by 32-column panels: the panel's top block by an
+//           then its pivot columns are factorised by 32-column panels: the panel's top block by an
 //           unscaled right-looking elimination in shared memory, the rows below by a per-row
-//           substitution against it, the trailing lower triangle by a rank-32 update in 64 x 64
-//           tiles staged in shared memory.  The front lives in global memory: the pivot columns
-//           (f x np, column-major) are the stored factor (L below the diagonal, D on it); the
-//           trailing nu x nu block is the update matrix for the parent.
+//           substitution against it, the remaining pivot columns by a rank-32 update in 64 x 64
+//           register tiles.  The update matrix for the parent then takes one symmetric rank-np
+//           update over all pivot columns (each 64 x 64 tile read and written once).  The front
+//           lives in global memory: the pivot columns (f x np, column-major) are the stored factor
+//           (L below the diagonal, D on it); the trailing nu x nu block is the update matrix.
 //   forward front vector = right-hand side at the pivots + the children's update vectors; the
 //           unit lower pivot block is solved by 32-row blocks (warp 0 by shuffles, the rows below
 //           by all threads); y = z / d goes to the solution, the rest to the update vector.
