@@ -374,9 +374,8 @@ st_status st_load_quadrature(st_fdm* h, int exact, int q_t, int q_x, void* F, vo
 
 /* ------------------------------------------------------------------ allocation-free residual */
 /* The FP64 residual of st_residual, for callers that must not allocate device memory while
- * they run: code calling it inside a CUDA stream capture in global mode (where cudaMalloc is a
- * prohibited call), frameworks that own all device memory through their own pool, and loops
- * that cannot take cudaMalloc's implicit device synchronisation.  It has no counterpart in the
+ * they run: frameworks that own all device memory through their own pool, and loops that cannot
+ * take cudaMalloc's implicit device synchronisation.  It has no counterpart in the
  * paper; it computes the same R = F~ - K (psi - 1 (x) psi0) as st_residual.
  * F, psi: device (n_t, n_x) c128; psi0: device n_x c128 or NULL; R: device (n_t, n_x) c128 output
  * or NULL (it may alias F but not psi or psi0: ST_ERR_ARG); norms: device double[2] output receiving ||R||_2^2 and ||F~||_2^2 (the caller divides;
@@ -385,8 +384,7 @@ st_status st_load_quadrature(st_fdm* h, int exact, int q_t, int q_x, void* F, vo
  * sums inside the library, resident on every device that loads it until the process exits.  The
  * limit is ceil(n_x/256) * ceil(n_t/16) <= 65536 (e.g. n_x = 65,025 with n_t <= 4096);
  * larger problems get ST_ERR_ARG.  The first call on a device looks up that array's device
- * address (cudaGetSymbolAddress, which may load the module): make the first call before any
- * stream capture.  All calls share the array: calls that overlap on the GPU (other streams or
+ * address (cudaGetSymbolAddress, which may load the module).  All calls share the array: calls that overlap on the GPU (other streams or
  * host threads) race and must be serialised by the caller. */
 st_status st_residual_noalloc(const st_fdm* h, const void* F, const void* psi0, const void* psi, void* R,
                               double* norms, void* stream);

@@ -1,10 +1,9 @@
 // st_residual_noalloc: the FP64 Kronecker residual with its norms, for callers that must
 // not allocate device memory while they run.
 //
-// Who needs it: code that calls the solver's residual from inside a CUDA stream capture
-// in global mode (cudaMalloc is a prohibited call there and fails the capture), code that
-// owns all device memory through its own pool and forbids driver allocations after start-up,
-// and loops that cannot afford cudaMalloc's implicit device-wide synchronisation.  The handle
+// Who needs it: code that owns all device memory through its own pool and forbids driver
+// allocations after start-up, and loops that cannot afford cudaMalloc's implicit device-wide
+// synchronisation.  The handle
 // (st_fdm_setup) is still created beforehand, at a point where allocating is fine.
 //
 // The only scratch the computation needs -- one pair of partial sums per thread block -- lives

@@ -1,9 +1,8 @@
 """The allocation-free residual entry point, st_residual_noalloc, called through the C ABI.
 
-Some callers cannot allocate device memory while they run: code recorded inside a global-mode
-stream capture, frameworks that own all device memory through their own pool, and loops that
-cannot take cudaMalloc's implicit device synchronisation.  For them the library offers the FP64
-residual with its scratch in a fixed device array.  These tests check it against st_residual on
+Some callers cannot allocate device memory while they run: frameworks that own all device memory
+through their own pool, and loops that cannot take cudaMalloc's implicit device synchronisation.
+For them the library offers the FP64 residual with its scratch in a fixed device array.  These tests check it against st_residual on
 the same inputs, twice in a row (the fixed array keeps the previous call's contents), within the
 residual parity tolerance; that repeated calls change neither torch's allocator nor the device's
 free memory; and that a size beyond the fixed array is refused.  The file is named to run after
